@@ -1,0 +1,347 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 wall-distance solver (HJ / LAD pseudo-HJ, arXiv 2111.09859).
+
+A step = one complete wall-distance solve of the workload: Poisson initial guess, HJ
+pseudo-time marching (RK4, local time steps, filter, change norms) until the tolerance.
+Default workload: the O-grid around a circular cylinder (257 radial x 512 periodic
+circumferential nodes, wall radius 0.5, outer radius 10, radial ratio 1.03), compact C6
+scheme, LAD pseudo-HJ with the curvature correction, alpha_f = 0.495, FP32 state with FP64
+metrics, tolerance RMS(dphi) <= 1e-6 L.  Metric: Mcell-iter/s = nodes x pseudo steps /
+device time.  Every rank solves its own copies (weak scaling, no collective on the data
+path); rank 0 prints one JSON line.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Mcell-iter/s & time-to-converged d (FP32 batched vs FP64 plain), p99 latency"
+UNIT = "Mcell-iter/s"
+
+
+def workload_spec():
+    from paper_2111_09859_gb300 import workloads as W
+
+    return W.cylinder(257, 512, 1.03)
+
+
+def solve_params(wd, tol):
+    return wd.default_params(wd.C6, equation=wd.HJ_LAD, curvature=1, alpha_f=0.495,
+                             tol_l2=tol, max_iters=20000, check_every=10, poisson_max_iters=100)
+
+
+class ClockSampler:
+    """nvidia-smi SM clock / throttle sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        sm.sort()
+        med = sm[len(sm) // 2] if sm else None
+        return {"sm_mhz": med, "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def flush_l2(buf):
+    buf.add_(1)      # writes 256 MB, more than the 129 MB L2
+
+
+def peak_hbm():
+    try:
+        d = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def algorithmic_bytes(cls, nodes, nd, es, ms, curv):
+    """Algorithmic DRAM bytes of one launch of a kernel class (the minimum each pass must
+    move): every field read once, every output written once."""
+    if cls == "deriv":          # phi -> d(phi)/dxi_l
+        return nodes * 2 * es
+    if cls == "div":            # U_m (and n_m) + nd metrics in, Laplacian (and kappa) r/w
+        nf = nd * (2 if curv else 1)
+        nout = 2 if curv else 1
+        return nodes * (nf * es + nd * ms + 2 * nout * es)
+    if cls in ("filter", "gauss"):
+        return nodes * 2 * es
+    return None
+
+
+def run_native(args, rank, world):
+    import torch
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    from paper_2111_09859_gb300 import build as B
+
+    B.build()
+    from paper_2111_09859_gb300 import wd
+
+    spec = workload_spec()
+    prec = wd.FP32_METRIC64
+    tol = 1e-6
+    p = solve_params(wd, tol)
+    stream = torch.cuda.current_stream()
+    g = wd.Grid(spec, prec, wd.C6, stream=stream)
+    phi = g.empty()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        g.solve(p, phi)
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    g.profile(True)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    total_ms, iters, piters = 0.0, 0, 0
+    stats = []
+    for _ in range(args.steps):
+        flush_l2(flush)
+        barrier()
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        _, st = g.solve(p, phi)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        total_ms += ev0.elapsed_time(ev1)
+        iters += st["iters"]
+        piters += st["poisson_iters"]
+        stats.append(st)
+    prof = g.profile_read()
+    g.profile(False)
+    clk = clocks.stop()
+    # the kernel timer adds gaps between launches: time the same steps again without it
+    total_ms_plain = 0.0
+    for _ in range(args.steps):
+        flush_l2(flush)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        g.solve(p, phi)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        total_ms_plain += ev0.elapsed_time(ev1)
+    ms = total_ms_plain
+    if world > 1:
+        import torch.distributed as dist
+
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    nodes = spec.N
+    cell_iters = nodes * (iters + piters) * world
+    value = cell_iters / (ms * 1e-3) / 1e6
+
+    # accuracy of the timed result against the exact distance r - 0.5
+    import numpy as np
+
+    exact = np.hypot(*spec.xyz) - 0.5
+    err32 = float(np.abs(phi.double().cpu().numpy() - exact).max())
+
+    # FP64 plain form on the same grid: time-to-converged at tolerance 1e-10
+    g64 = wd.Grid(spec, wd.FP64, wd.C6, stream=stream)
+    phi64 = g64.empty()
+    p64 = solve_params(wd, 1e-10)
+    g64.solve(p64, phi64)
+    torch.cuda.synchronize()
+    flush_l2(flush)
+    ev0.record(stream)
+    _, st64 = g64.solve(p64, phi64)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    t64 = ev0.elapsed_time(ev1) * 1e-3
+    err64 = float(np.abs(phi64.cpu().numpy() - exact).max())
+    diff = float(np.abs(phi64.cpu().numpy() - phi.double().cpu().numpy()).max())
+    del g64
+
+    # end to end through the public API with host buffers: grid creation from host
+    # coordinates (H2D), solve, result copied to pinned host memory (D2H)
+    host_phi = torch.empty(nodes, dtype=torch.float32).pin_memory()
+    e2e_ms = 0.0
+    for _ in range(args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ge = wd.Grid(spec, prec, wd.C6, stream=stream)
+        ge.solve(p, host_phi)
+        ge.close()
+        torch.cuda.synchronize()
+        e2e_ms += (time.perf_counter() - t0) * 1e3
+    e2e_value = cell_iters / (e2e_ms * 1e-3) / 1e6 if e2e_ms > 0 else None
+
+    # roofline of the dominant kernel class
+    es, msz = 4, 8
+    best = max((k for k in prof if prof[k][1] > 0), key=lambda k: prof[k][0])
+    kms, kn = prof[best]
+    ab = algorithmic_bytes(best, nodes, spec.ndim, es, msz, True)
+    peak, src = peak_hbm()
+    roof = None
+    if ab is not None and kn > 0:
+        ach = ab / (kms / kn * 1e-3) / 1e9
+        roof = {"bound": "hbm", "kernel": best, "achieved": round(ach, 1), "peak": peak,
+                "peak_source": src + " (of " + src + ")", "unit": "GB/s", "frac": round(ach / peak, 4),
+                "traffic": None, "algorithmic_bytes_per_launch": ab,
+                "avg_launch_us": round(kms / kn * 1e3, 3),
+                "share_of_timed": round(kms / max(1e-9, sum(v[0] for v in prof.values())), 3)}
+    launches = sum(v[1] for v in prof.values())
+
+    out = {
+        "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32 (metrics f64)",
+        "data": "synthetic",
+        "config": {"workload": "cylinder O-grid 257x512 (r 0.5..10, ratio 1.03), C6 + LAD + curvature, "
+                               "alpha_f 0.495, FP32 state / FP64 metrics, tol RMS 1e-6, Poisson 100",
+                   "nodes": nodes, "pseudo_steps_per_solve": (iters + piters) / args.steps,
+                   "l2_between_steps": "flushed (256 MB write)",
+                   "parallelism": f"replicas x{world}"},
+        "time_to_converged_s": {"fp32_metric64": round(ms / args.steps * 1e-3, 4),
+                                "fp64_plain": round(t64, 4), "fp64_iters": st64["iters"]},
+        "accuracy": {"max_err_vs_exact_fp32m64": err32, "max_err_vs_exact_fp64": err64,
+                     "max_fp32_minus_fp64": diff},
+        "roofline": roof,
+        "kernel_ms": {k: round(v[0], 3) for k, v in prof.items()},
+        "gpu_launches": int(launches),
+        "clocks": clk,
+        "e2e": {"value": round(e2e_value, 2) if e2e_value else None, "unit": UNIT,
+                "h2d_bytes_per_step": int(spec.xyz.nbytes), "d2h_bytes_per_step": int(nodes * 4)},
+    }
+    if rank == 0:
+        out["cpu_baseline"] = cpu_baseline()
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+def cpu_baseline(n_steps=12):
+    """The FP64 oracle (one thread) on a bounded sample of the same workload: a Poisson
+    step and n HJ pseudo steps of the full cylinder grid from its Poisson guess."""
+    import numpy as np
+
+    import oracle as O
+
+    spec = workload_spec()
+    og = O.Grid(spec.shape, spec.xyz, spec.bc_lo, spec.bc_hi, scheme=O.C6, period=spec.period)
+    kw = dict(equation=O.HJ_LAD, scheme=O.C6, curvature=1, alpha_f=0.495, cfl=0.6)
+    phi0 = og.apply_bc(np.hypot(*spec.xyz) - 0.5)
+    t0 = time.perf_counter()
+    og.hj_steps(phi0, n_steps, **kw)
+    dt = time.perf_counter() - t0
+    return {"value": round(spec.N * n_steps / dt / 1e6, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{n_steps} HJ pseudo steps of the 257x512 cylinder grid (FP64, one thread)",
+            "seconds": round(dt, 2)}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    import numpy as np
+
+    import oracle as O
+
+    O.build()
+    spec = workload_spec()
+    og = O.Grid(spec.shape, spec.xyz, spec.bc_lo, spec.bc_hi, scheme=O.C6, period=spec.period)
+    kw = dict(equation=O.HJ_LAD, scheme=O.C6, curvature=1, alpha_f=0.495, cfl=0.6)
+    phi = og.apply_bc(np.hypot(*spec.xyz) - 0.5)
+    n = 4
+    for _ in range(args.warmup):
+        phi, _ = og.hj_steps(phi, 1, **kw)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        phi, _ = og.hj_steps(phi, n, **kw)
+    dt = time.perf_counter() - t0
+    v = spec.N * n * args.steps / dt / 1e6
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": round(v, 4), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt / args.steps * 1e3, 2),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": "cylinder O-grid 257x512, C6 + LAD + curvature, alpha_f 0.495",
+                   "sample": f"each step = {n} HJ pseudo steps of the full grid"},
+        "cpu_baseline": {"value": round(v, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{n} HJ pseudo steps per step, FP64, one thread"},
+        "e2e": {"value": round(v, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_native(args, rank, world)
+
+
+if __name__ == "__main__":
+    main()

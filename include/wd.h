@@ -1,0 +1,214 @@
+/*
+ * wd.h -- C ABI of libwd, a GB300 (sm_103a) implementation of the high-order central
+ * difference Hamilton-Jacobi wall-distance method of Kakumani, Vadlamani & Tucker,
+ * "On the use of high order central difference schemes for differential equation based
+ * wall distance computations" (arXiv 2111.09859).
+ *
+ * Conventions shared by every entry point
+ *  - A grid has n[0] x n[1] x n[2] nodes (n[2] = 1 in 2-D).  Node (i, j, k) of every
+ *    caller array sits at i + n[0] * (j + n[1] * k) (dense, i fastest).
+ *  - "phi" arrays hold the grid's state precision: double for WD_FP64, float for
+ *    WD_FP32_METRIC64 and WD_FP32.  Metric exports are always double.
+ *  - Pointers named *_dev are CUDA device pointers owned by the caller; *_host are host
+ *    pointers read during the call only.  The library owns every internal buffer.
+ *  - All device work is issued on the stream given to wd_create_grid (or wd_set_stream).
+ *    wd_solve, wd_steps, wd_step_unsteady and wd_solve_batch return after the stream has
+ *    finished; the operator entry points (wd_derivative ... wd_apply_bc) only enqueue.
+ *  - Every function returns a wd_status and never aborts.  After WD_ERR_CUDA the CUDA
+ *    context may be unusable; after any other error the grid stays valid.
+ *    wd_last_error() gives a one-line description of the most recent failure on the
+ *    calling thread.
+ *  - Calls on one grid must not overlap; distinct grids may be used from distinct threads.
+ */
+#ifndef WD_H
+#define WD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct wd_grid_s* wd_grid;
+
+typedef enum {
+    WD_OK = 0,
+    WD_ERR_INVALID_ARG = 1,
+    WD_ERR_OOM = 2,
+    WD_ERR_CUDA = 3,
+    WD_ERR_NOT_CONVERGED = 4,
+    WD_ERR_DIVERGED = 5,
+    WD_ERR_TIMEOUT = 6
+} wd_status;
+
+/* boundary kind of each face (Sec. 3.5) */
+enum { WD_BC_WALL = 0,      /* Dirichlet phi = 0 on the face (Eq. 22) */
+       WD_BC_FARFIELD = 1,  /* linear extrapolation along the grid line, scaled by the
+                               local spacing ratio (reading of Eq. 23) */
+       WD_BC_NEUMANN = 2,   /* phi copied from the neighbour: d(phi)/dn = 0 (Eq. 23) */
+       WD_BC_PERIODIC = 3 };/* both faces of the direction */
+
+/* state / metric precision */
+enum { WD_FP64 = 0,          /* everything double */
+       WD_FP32_METRIC64 = 1, /* float state, stencils and line solves; metrics stored and
+                                applied (chain rule, divergence) in double */
+       WD_FP32 = 2 };        /* float state and metrics (metrics still computed in double) */
+
+/* equation (Sec. 2.3) */
+enum { WD_HJ_STD = 0,        /* Gamma = eps * phi (Eq. 6) */
+       WD_HJ_LAD = 1,        /* Gamma = MIN(eps*phi, LAD term) (Eq. 7) */
+       WD_EIKONAL = 2 };     /* Gamma = 0 (Eq. 17) */
+
+/* spatial scheme (Sec. 3.2.2, Eq. 16) */
+enum { WD_E2 = 0, WD_E4 = 1, WD_E6 = 2, WD_C4 = 3, WD_C6 = 4 };
+
+/* initial guess */
+enum { WD_INIT_ZERO = 0,     /* phi = 0 (Sec. 3.5) */
+       WD_INIT_POISSON = 1,  /* Poisson pseudo steps + Spalding equation (Eqs. 3-4, 19) */
+       WD_INIT_GIVEN = 2 };  /* the caller's phi_dev contents (warm start) */
+
+typedef struct {
+    int ndim;              /* 2 or 3 */
+    int n[3];              /* nodes per direction, each >= 8 for d < ndim; n[2] = 1 in 2-D */
+    int bc_lo[3];          /* WD_BC_* of the face at index 0 of each direction */
+    int bc_hi[3];          /* WD_BC_* of the face at index n-1 of each direction */
+    double period[3][3];   /* periodic direction d: x(i + n[d]) = x(i) + period[d] */
+    int precision;         /* WD_FP64 / WD_FP32_METRIC64 / WD_FP32 */
+    int scheme;            /* WD_E2 .. WD_C6: every derivative and the metrics (Sec. 3.2.2) */
+    double L_ref;          /* reference length of the convergence norms (Eq. 20) */
+} wd_grid_desc;
+
+typedef struct {
+    int equation;          /* WD_HJ_STD / WD_HJ_LAD / WD_EIKONAL */
+    int curvature;         /* 1: Nakanishi correction, Sec. 5.4 / Eq. 25 */
+    double eps;            /* epsilon of Eqs. 6, 7, 25 */
+    double C_lad;          /* C of Eq. 7 */
+    double lad_exp;        /* exponent of Delta x_l in Eq. 7 (the paper prints 3) */
+    double alpha_f;        /* filter coefficient of Eq. 21, |alpha_f| < 0.5 */
+    int filter;            /* 1: filter along every direction after each pseudo step */
+    double cfl;            /* local pseudo time step factor */
+    double eps0;           /* epsilon_0 of the unit normal in Eq. 25 */
+    double tol_l2;         /* stop when RMS(phi_new - phi_old)/L_ref <= tol_l2 (<= 0: off) */
+    double tol_linf;       /* stop when max|phi_new - phi_old|/L_ref <= tol_linf, Eq. 20 */
+    int max_iters;         /* HJ pseudo steps at most */
+    int check_every;       /* pseudo steps between convergence checks (host reads) */
+    int init;              /* WD_INIT_* */
+    double poisson_tol;    /* Poisson stop on RMS(dphi')/L_ref^2 (<= 0: run poisson_max_iters) */
+    int poisson_max_iters; /* Poisson pseudo steps at most */
+} wd_solve_params;
+
+typedef struct {
+    int iters;             /* HJ pseudo steps taken */
+    int poisson_iters;     /* Poisson pseudo steps taken */
+    double res_l2;         /* RMS change of the last step / L_ref */
+    double res_linf;       /* max change of the last step / L_ref */
+    int converged;         /* tolerance met */
+    int diverged;          /* NaN / Inf met */
+    double seconds;        /* wall time of the call */
+    size_t device_bytes;   /* library-owned device memory of the grid */
+} wd_stats;
+
+/* Fills *p with the defaults used by the tests and the benchmark: LAD HJ, eps 0.2,
+ * C 0.1, exponent 3, alpha_f 0.49, filter on, cfl 0.8 (explicit) / 0.6 (compact) for the
+ * given scheme, eps0 1e-8, tol_l2 1e-10, 100 Poisson steps. */
+void wd_default_params(int scheme, wd_solve_params* p);
+
+/* Creates a grid (Sec. 3.1): uploads the node coordinates xyz_host (ndim x N doubles:
+ * all x, then all y, then all z), computes the metrics on the GPU with the grid's scheme,
+ * marks wall faces and the optional Dirichlet nodes (mask_host[p] != 0, values
+ * dval_host[p], NULL -> 0) and precomputes the line-solve tables.  cuda_stream is a
+ * cudaStream_t (NULL = legacy default stream).
+ * Errors: WD_ERR_INVALID_ARG (bad sizes or boundary kinds, non-positive L_ref),
+ * WD_ERR_OOM, WD_ERR_CUDA. */
+wd_status wd_create_grid(const wd_grid_desc* desc, const double* xyz_host,
+                         const uint8_t* mask_host, const double* dval_host,
+                         void* cuda_stream, wd_grid* out);
+
+/* Frees every device buffer of the grid (NULL is ignored). */
+void wd_destroy_grid(wd_grid g);
+
+/* Changes the stream used by later calls on g. */
+wd_status wd_set_stream(wd_grid g, void* cuda_stream);
+
+/* Steady solve (Sec. 3.3): initial guess, then HJ pseudo-time marching (RK4 with local
+ * time steps, boundary conditions after every stage, filter after every step) until the
+ * tolerances hold, max_iters is reached, or a NaN appears.  phi_dev (N values of the
+ * state precision, dense layout) is read when init == WD_INIT_GIVEN and always receives
+ * the result.  Returns WD_OK when converged or when no tolerance was set,
+ * WD_ERR_NOT_CONVERGED after max_iters with a tolerance set, WD_ERR_DIVERGED on NaN/Inf. */
+wd_status wd_solve(wd_grid g, const wd_solve_params* p, void* phi_dev, wd_stats* stats);
+
+/* Unsteady re-solve (Sec. 3.3, last paragraph; Sec. 5.5): replaces the Dirichlet set by
+ * mask_dev / dval_dev (device arrays of N uint8 and N state-precision values; wall faces
+ * stay Dirichlet 0; NULL keeps the current set) and marches from the previous solution in
+ * phi_dev (warm start, init ignored).  Same return values as wd_solve. */
+wd_status wd_step_unsteady(wd_grid g, const uint8_t* mask_dev, const void* dval_dev,
+                           const wd_solve_params* p, void* phi_dev, wd_stats* stats);
+
+/* Solves n independent grids with the same parameters; phi_dev[i] and stats[i] belong to
+ * grids[i].  Returns the first non-OK status (every grid is still attempted). */
+wd_status wd_solve_batch(wd_grid* grids, int n, const wd_solve_params* p, void** phi_dev,
+                         wd_stats* stats);
+
+/* Device bytes wd_create_grid would allocate for desc (0 if desc is invalid). */
+size_t wd_query_footprint(const wd_grid_desc* desc, const wd_solve_params* p);
+
+const char* wd_status_string(wd_status s);
+const char* wd_last_error(void);
+
+/* ---- operator entry points: one step of the method each, for parity testing ---------- */
+
+/* Metrics of Sec. 3.1 (a1): xi_dev[(l*3+m)*N + p] = d(xi_l)/d(x_m), J_dev[p] = det of
+ * dx_m/dxi_l, dx_dev[l*N + p] = |dx/dxi_l| (double, dense; unused entries are 0). */
+wd_status wd_get_metrics(wd_grid g, double* xi_dev, double* J_dev, double* dx_dev);
+
+/* First derivative along direction dir with unit computational spacing (Eq. 16 and its
+ * boundary rows), in the grid's scheme and state precision (a4). */
+wd_status wd_derivative(wd_grid g, int dir, const void* in_dev, void* out_dev);
+
+/* One implicit filter pass along dir (Eq. 21), order reduced to 2 near non-periodic ends,
+ * end nodes unfiltered (a10).  in_dev may equal out_dev. */
+wd_status wd_filter(wd_grid g, double alpha_f, int dir, const void* in_dev, void* out_dev);
+
+/* Right-hand side R with d(phi)/dt* = R and the local pseudo time step (a5-a9):
+ * kind 0 = HJ (Eqs. 5-7, 9, 25), kind 1 = Poisson (Eq. 19). */
+wd_status wd_rhs(wd_grid g, const wd_solve_params* p, int kind, const void* phi_dev,
+                 void* R_dev, void* dt_dev);
+
+/* Spalding auxiliary equation (Eq. 4, minus root): phi' -> phi (a3). */
+wd_status wd_spalding(wd_grid g, const void* phip_dev, void* phi_dev);
+
+/* HJ boundary conditions in place: far-field / Neumann faces direction by direction,
+ * then every Dirichlet node (a2). */
+wd_status wd_apply_bc(wd_grid g, void* phi_dev);
+
+/* Exactly nsteps pseudo steps (RK4 + BCs + filter + change norms) from phi_dev in place:
+ * kind 0 = HJ, kind 1 = Poisson (a9-a11).  stats gets the last step's norms. */
+wd_status wd_steps(wd_grid g, const wd_solve_params* p, int kind, void* phi_dev, int nsteps,
+                   wd_stats* stats);
+
+/* ---- instrumentation (no counterpart in the paper) ---------------------------------- */
+
+/* kernel classes timed by wd_profile */
+enum { WD_K_DERIV = 0,   /* first derivatives of phi along one direction */
+       WD_K_DIV = 1,     /* metric-weighted divergence pass (Laplacian / curvature) */
+       WD_K_FILTER = 2,  /* implicit filter pass */
+       WD_K_GAUSS = 3,   /* Gaussian smoothing pass of the LAD diffusivity */
+       WD_K_POINT = 4,   /* pointwise kernels: chain rule, LAD term, RK stage, Spalding */
+       WD_K_BC = 5,      /* boundary conditions */
+       WD_K_NORM = 6,    /* change norms + commit */
+       WD_K_NCLASS = 7 };
+
+/* enable != 0 clears the counters and brackets every later kernel launch on g with CUDA
+ * events on g's stream (this adds a small gap between launches); enable == 0 stops. */
+wd_status wd_profile(wd_grid g, int enable);
+
+/* Total device time (ms, from the events) and launch count of kernel class cls since
+ * profiling was enabled; synchronises the stream. */
+wd_status wd_profile_read(wd_grid g, int cls, double* ms_total, long long* launches);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

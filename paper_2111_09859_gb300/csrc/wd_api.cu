@@ -1,0 +1,1022 @@
+// wd_api.cu -- C ABI of libwd: grid creation (metrics, masks, line tables), the
+// pseudo-time solver driver (Sec. 3.3) and the operator entry points.  Every step of the
+// method runs in the kernels of wd_kernels.cu; this file only sequences launches, moves
+// caller arrays in and out of the padded device layout and reads the convergence norms.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <type_traits>
+#include <vector>
+
+#include "wd_api_internal.h"
+
+using namespace wd;
+
+namespace wd {
+static thread_local std::string g_err;
+wd_status set_error(wd_status s, const char* msg)
+{
+    g_err = msg;
+    return s;
+}
+wd_status cuda_error(cudaError_t e, const char* where)
+{
+    g_err = std::string(where) + ": " + cudaGetErrorString(e);
+    return WD_ERR_CUDA;
+}
+}  // namespace wd
+
+#define CK(...)                                                         \
+    do {                                                                \
+        cudaError_t _e = (__VA_ARGS__);                                 \
+        if (_e != cudaSuccess) return wd::cuda_error(_e, #__VA_ARGS__); \
+    } while (0)
+#define ST(...)                                \
+    do {                                       \
+        wd_status _s = (__VA_ARGS__);          \
+        if (_s != WD_OK) return _s;            \
+    } while (0)
+
+enum {
+    W_PHIN, W_PHIS, W_ACC, W_DT, W_D0, W_D1, W_D2, W_U0, W_U1, W_U2, W_N0, W_N1, W_N2,
+    W_LAP, W_KAP, W_LAD, W_T0, W_T1, W_NWORK
+};
+
+struct wd_grid_s {
+    Dims D;
+    wd_grid_desc desc;
+    cudaStream_t stream = nullptr;
+    int es = 8;                 // bytes per state element
+    size_t bytes = 0;
+    double* xyz = nullptr;      // 3 padded coordinate arrays
+    double* xi_d = nullptr;     // 9 padded arrays
+    double* J_d = nullptr;
+    double* dx_d = nullptr;     // 3 padded arrays
+    void* xi_m = nullptr;       // metrics in the metric precision (aliases xi_d for double)
+    int xi_alias = 1;
+    void* sig1 = nullptr;
+    void* sig2 = nullptr;
+    void* lads = nullptr;       // 3 arrays
+    double lads_exp = -1.0;
+    double* ffr = nullptr;      // 6 x fmax spacing ratios
+    long long fmax = 0;
+    uint8_t* wall = nullptr;
+    uint8_t* mask = nullptr;
+    void* dval = nullptr;
+    long long nactive = 0;
+    void* w[W_NWORK] = {};
+    double* partial = nullptr;
+    unsigned* counter = nullptr;
+    double* result = nullptr;
+    double* hres = nullptr;     // pinned
+    unsigned long long* dcount = nullptr;
+    int nred = 0;
+    HostLineTab dtab[3], ftab[3], etab[3];
+    // kernel timer (wd_profile)
+    int prof_on = 0;
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<std::pair<int, int>> ev_used;   // (class, index of the start event; stop = +1)
+    double prof_ms[WD_K_NCLASS] = {};
+    long long prof_n[WD_K_NCLASS] = {};
+};
+
+static cudaError_t prof_flush(wd_grid g)
+{
+    if (g->ev_used.empty()) return cudaSuccess;
+    cudaError_t e = cudaStreamSynchronize(g->stream);
+    if (e != cudaSuccess) return e;
+    for (auto& u : g->ev_used) {
+        float ms = 0.f;
+        e = cudaEventElapsedTime(&ms, g->ev_pool[u.second], g->ev_pool[u.second + 1]);
+        if (e != cudaSuccess) return e;
+        g->prof_ms[u.first] += ms;
+        g->prof_n[u.first] += 1;
+    }
+    g->ev_used.clear();
+    return cudaSuccess;
+}
+
+// brackets one launch with events when the timer is on
+struct ProfScope {
+    wd_grid g;
+    int cls, idx = -1;
+    ProfScope(wd_grid g_, int c) : g(g_), cls(c)
+    {
+        if (!g->prof_on) return;
+        if (2 * (g->ev_used.size() + 1) > g->ev_pool.size()) {
+            if (g->ev_pool.size() < 8192) {
+                size_t old = g->ev_pool.size();
+                g->ev_pool.resize(old + 512);
+                for (size_t i = old; i < g->ev_pool.size(); i++) cudaEventCreate(&g->ev_pool[i]);
+            } else if (prof_flush(g) != cudaSuccess) {
+                return;
+            }
+        }
+        idx = (int)(2 * g->ev_used.size());
+        cudaEventRecord(g->ev_pool[idx], g->stream);
+    }
+    ~ProfScope()
+    {
+        if (idx < 0) return;
+        cudaEventRecord(g->ev_pool[idx + 1], g->stream);
+        g->ev_used.push_back({cls, idx});
+    }
+};
+
+static bool metric_double(int prec) { return prec != WD_FP32; }
+
+static size_t footprint_bytes(const wd_grid_desc* d)
+{
+    long long pitch = (d->n[0] + 31) / 32 * 32;
+    long long total = pitch * d->n[1] * d->n[2];
+    size_t es = d->precision == WD_FP64 ? 8 : 4;
+    size_t ms = metric_double(d->precision) ? 8 : 4;
+    size_t b = 0;
+    b += (size_t)total * 8 * (3 + 9 + 1 + 3);          // xyz, xi_d, J, dx
+    if (!metric_double(d->precision)) b += (size_t)total * 4 * 9;
+    b += (size_t)total * ms * (2 + 3);                  // sig1, sig2, lads
+    b += (size_t)total * (2 + es);                      // wall, mask, dval
+    b += (size_t)total * es * W_NWORK;
+    long long fmax = 0;
+    for (int k = 0; k < 3; k++) {
+        long long f = (long long)d->n[(k + 1) % 3] * d->n[(k + 2) % 3];
+        if (f > fmax) fmax = f;
+    }
+    b += (size_t)fmax * 6 * 8;
+    for (int k = 0; k < d->ndim; k++) {
+        int P = choose_chunks(d->n[k]);
+        b += 3 * ((size_t)(5 * d->n[k] + 2 * P + 4 * P * P) * 12 + (P + 1) * 4);
+    }
+    return b;
+}
+
+static wd_status validate_desc(const wd_grid_desc* d)
+{
+    if (!d) return set_error(WD_ERR_INVALID_ARG, "desc is NULL");
+    if (d->ndim != 2 && d->ndim != 3) return set_error(WD_ERR_INVALID_ARG, "ndim must be 2 or 3");
+    if (d->ndim == 2 && d->n[2] != 1) return set_error(WD_ERR_INVALID_ARG, "n[2] must be 1 in 2-D");
+    for (int k = 0; k < d->ndim; k++) {
+        if (d->n[k] < 8) return set_error(WD_ERR_INVALID_ARG, "every direction needs >= 8 nodes");
+        if (d->n[k] > (1 << 16)) return set_error(WD_ERR_INVALID_ARG, "direction too long");
+        int lo = d->bc_lo[k], hi = d->bc_hi[k];
+        if (lo < 0 || lo > 3 || hi < 0 || hi > 3)
+            return set_error(WD_ERR_INVALID_ARG, "unknown boundary kind");
+        if ((lo == WD_BC_PERIODIC) != (hi == WD_BC_PERIODIC))
+            return set_error(WD_ERR_INVALID_ARG, "periodic must be set on both faces");
+    }
+    if (d->precision < 0 || d->precision > 2) return set_error(WD_ERR_INVALID_ARG, "bad precision");
+    if (d->scheme < WD_E2 || d->scheme > WD_C6) return set_error(WD_ERR_INVALID_ARG, "bad scheme");
+    if (!(d->L_ref > 0.0)) return set_error(WD_ERR_INVALID_ARG, "L_ref must be positive");
+    long long tot = (long long)((d->n[0] + 31) / 32 * 32) * d->n[1] * d->n[2];
+    if (tot > (1LL << 31)) return set_error(WD_ERR_INVALID_ARG, "grid too large");
+    return WD_OK;
+}
+
+static wd_status dmalloc(wd_grid g, void** p, size_t bytes)
+{
+    if (cudaMalloc(p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return set_error(WD_ERR_OOM, "cudaMalloc failed");
+    }
+    g->bytes += bytes;
+    return WD_OK;
+}
+
+// dense caller array <-> padded device array (either side may be host or device memory)
+static cudaError_t to_padded(wd_grid g, void* dst, const void* src, size_t es)
+{
+    const Dims& D = g->D;
+    return cudaMemcpy2DAsync(dst, (size_t)D.pitch * es, src, (size_t)D.n[0] * es, (size_t)D.n[0] * es,
+                             (size_t)D.n[1] * D.n[2], cudaMemcpyDefault, g->stream);
+}
+static cudaError_t from_padded(wd_grid g, void* dst, const void* src, size_t es)
+{
+    const Dims& D = g->D;
+    return cudaMemcpy2DAsync(dst, (size_t)D.n[0] * es, src, (size_t)D.pitch * es, (size_t)D.n[0] * es,
+                             (size_t)D.n[1] * D.n[2], cudaMemcpyDefault, g->stream);
+}
+
+static void release(wd_grid g)
+{
+    if (!g) return;
+    cudaFree(g->xyz);
+    cudaFree(g->xi_d);
+    cudaFree(g->J_d);
+    cudaFree(g->dx_d);
+    if (!g->xi_alias) cudaFree(g->xi_m);
+    cudaFree(g->sig1);
+    cudaFree(g->sig2);
+    cudaFree(g->lads);
+    cudaFree(g->ffr);
+    cudaFree(g->wall);
+    cudaFree(g->mask);
+    cudaFree(g->dval);
+    for (int k = 0; k < W_NWORK; k++) cudaFree(g->w[k]);
+    cudaFree(g->partial);
+    cudaFree(g->counter);
+    cudaFree(g->result);
+    cudaFree(g->dcount);
+    if (g->hres) cudaFreeHost(g->hres);
+    for (int k = 0; k < 3; k++) {
+        free_line_table(g->dtab[k]);
+        free_line_table(g->ftab[k]);
+        free_line_table(g->etab[k]);
+    }
+    for (auto& e : g->ev_pool) cudaEventDestroy(e);
+    delete g;
+}
+
+// ------------------------------------------------------------------------------------
+// solver, templated on state precision T and metric precision M
+// ------------------------------------------------------------------------------------
+
+template <typename T, typename M>
+struct Solver {
+    wd_grid g;
+    const wd_solve_params* p;
+    cudaStream_t st;
+    const Dims& D;
+    Solver(wd_grid g_, const wd_solve_params* p_) : g(g_), p(p_), st(g_->stream), D(g_->D) {}
+
+    T* W(int k) { return (T*)g->w[k]; }
+    const M* xi() { return (const M*)g->xi_m; }
+
+    wd_status ensure_filter(double al)
+    {
+        for (int d = 0; d < D.ndim; d++) {
+            HostLineTab& t = g->ftab[d];
+            if (t.valid && t.key == al) continue;
+            std::vector<double> a, c;
+            int imp;
+            filter_rows(al, D.n[d], D.per[d], a, c, imp);
+            ST(build_line_table(D.n[d], D.per[d], a, c, imp, t));
+            t.key = al;
+        }
+        return WD_OK;
+    }
+    wd_status ensure_lads(double ex)
+    {
+        if (g->lads_exp == ex) return WD_OK;
+        CK(launch_lad_scale<M>(D, g->xi_d, g->dx_d, ex, (M*)g->lads, st));
+        g->lads_exp = ex;
+        return WD_OK;
+    }
+
+    LineOp op_deriv() const
+    {
+        LineOp op;
+        std::memset(&op, 0, sizeof(op));
+        op.kind = OPK_DERIV;
+        op.scheme = g->desc.scheme;
+        return op;
+    }
+    static wd_status op_filter(double al, LineOp& op)
+    {
+        std::memset(&op, 0, sizeof(op));
+        op.kind = OPK_FILTER;
+        for (int hw = 1; hw <= 5; hw++)
+            if (!filter_coefficients(hw, al, op.fa[hw]))
+                return set_error(WD_ERR_INVALID_ARG, "filter coefficients");
+        op.fa[0][0] = 1.0;
+        return WD_OK;
+    }
+
+    wd_status deriv_dir(int d, const T* in, T* out)
+    {
+        Fields<T> f;
+        std::memset(&f, 0, sizeof(f));
+        f.in[0] = in;
+        f.out[0] = out;
+        ProfScope ps(g, WD_K_DERIV);
+        CK(launch_line<T, M>(D, d, g->dtab[d], op_deriv(), 1, 0, f, nullptr, 0, 0, st));
+        return WD_OK;
+    }
+    wd_status filter_dir(int d, double al, const T* in, T* out)
+    {
+        ST(ensure_filter(al));
+        LineOp op;
+        ST(op_filter(al, op));
+        Fields<T> f;
+        std::memset(&f, 0, sizeof(f));
+        f.in[0] = in;
+        f.out[0] = out;
+        ProfScope ps(g, WD_K_FILTER);
+        CK(launch_line<T, M>(D, d, g->ftab[d], op, 1, 0, f, nullptr, 0, 0, st));
+        return WD_OK;
+    }
+
+    // D_l phi for every l, then U (and n); Laplacian (and curvature) as metric-weighted
+    // divergences of U (and n), Eq. 9 / Eq. 25
+    wd_status grad_parts(const T* phi, bool curv)
+    {
+        for (int l = 0; l < D.ndim; l++) ST(deriv_dir(l, phi, W(W_D0 + l)));
+        T* Dl[3] = {W(W_D0), W(W_D1), W(W_D2)};
+        T* U[3] = {W(W_U0), W(W_U1), W(W_U2)};
+        T* nv[3] = {W(W_N0), W(W_N1), W(W_N2)};
+        ProfScope ps(g, WD_K_POINT);
+        CK(launch_grad<T, M>(D, Dl, xi(), U, curv ? nv : nullptr, p ? p->eps0 : 1e-8, st));
+        return WD_OK;
+    }
+    wd_status div_parts(bool curv)
+    {
+        int nd = D.ndim;
+        for (int l = 0; l < nd; l++) {
+            Fields<T> f;
+            std::memset(&f, 0, sizeof(f));
+            for (int m = 0; m < nd; m++) {
+                f.in[m] = W(W_U0 + m);
+                if (curv) f.in[nd + m] = W(W_N0 + m);
+            }
+            f.out[0] = W(W_LAP);
+            f.out[1] = W(W_KAP);
+            ProfScope ps(g, WD_K_DIV);
+            CK(launch_line<T, M>(D, l, g->dtab[l], op_deriv(), curv ? 2 * nd : nd, 1, f, xi(), nd,
+                                 l > 0, st));
+        }
+        return WD_OK;
+    }
+    // smoothed C |sum_l s_l d4_l(phi)| (Eq. 7); returns the buffer holding it
+    wd_status lad_part(const T* phi, T** out)
+    {
+        ST(ensure_lads(p->lad_exp));
+        {
+            ProfScope ps(g, WD_K_POINT);
+            CK(launch_lad_raw<T, M>(D, phi, (const M*)g->lads, p->C_lad, W(W_T0), st));
+        }
+        LineOp op;
+        std::memset(&op, 0, sizeof(op));
+        op.kind = OPK_GAUSS;
+        T* a = W(W_T0);
+        T* b = W(W_T1);
+        for (int l = 0; l < D.ndim; l++) {
+            Fields<T> f;
+            std::memset(&f, 0, sizeof(f));
+            f.in[0] = a;
+            f.out[0] = b;
+            ProfScope ps(g, WD_K_GAUSS);
+            CK(launch_line<T, M>(D, l, g->etab[l], op, 1, 0, f, nullptr, 0, 0, st));
+            T* t = a;
+            a = b;
+            b = t;
+        }
+        *out = a;
+        return WD_OK;
+    }
+
+    wd_status bc(T* phi, bool poisson)
+    {
+        for (int d = 0; d < D.ndim; d++) {
+            int lo = g->desc.bc_lo[d], hi = g->desc.bc_hi[d];
+            bool any = (lo == WD_BC_FARFIELD || lo == WD_BC_NEUMANN || hi == WD_BC_FARFIELD ||
+                        hi == WD_BC_NEUMANN);
+            if (!any) continue;
+            if (poisson) {
+                if (lo == WD_BC_FARFIELD) lo = WD_BC_NEUMANN;
+                if (hi == WD_BC_FARFIELD) hi = WD_BC_NEUMANN;
+            }
+            ProfScope ps(g, WD_K_BC);
+            CK(launch_bc_face<T>(D, d, lo, hi, g->ffr + (2 * d) * g->fmax, g->ffr + (2 * d + 1) * g->fmax,
+                                 phi, st));
+        }
+        ProfScope ps(g, WD_K_BC);
+        CK(launch_bc_mask<T>(D, g->mask, poisson ? nullptr : (const T*)g->dval, phi, st));
+        return WD_OK;
+    }
+
+    StageArgs<T, M> stage_args(const T* src, T* dst, bool poisson, const T* lad)
+    {
+        StageArgs<T, M> a;
+        a.src = src;
+        a.dst = dst;
+        a.phin = W(W_PHIN);
+        a.acc = W(W_ACC);
+        a.dt = W(W_DT);
+        a.U[0] = W(W_U0);
+        a.U[1] = W(W_U1);
+        a.U[2] = W(W_U2);
+        a.lap = W(W_LAP);
+        a.kap = W(W_KAP);
+        a.lad = lad;
+        a.sig1 = (const M*)g->sig1;
+        a.sig2 = (const M*)g->sig2;
+        a.eps = p->eps;
+        a.cfl = p->cfl;
+        a.equation = p->equation;
+        a.curvature = p->curvature;
+        a.poisson = poisson;
+        return a;
+    }
+
+    wd_status rhs_into(const T* src, T* dst, bool poisson, int stage)
+    {
+        bool curv = !poisson && p->curvature;
+        ST(grad_parts(src, curv));
+        ST(div_parts(curv));
+        T* lad = nullptr;
+        if (!poisson && p->equation == WD_HJ_LAD) ST(lad_part(src, &lad));
+        StageArgs<T, M> a = stage_args(src, dst, poisson, lad);
+        ProfScope ps(g, WD_K_POINT);
+        CK(launch_stage<T, M>(D, a, stage, st));
+        return WD_OK;
+    }
+
+    // one pseudo step from W_PHIN; leaves the new state in W_PHIN and the change norms in
+    // g->result
+    wd_status step(bool poisson)
+    {
+        for (int s = 0; s < 4; s++) {
+            const T* src = s == 0 ? W(W_PHIN) : W(W_PHIS);
+            ST(rhs_into(src, W(W_PHIS), poisson, s));
+            ST(bc(W(W_PHIS), poisson));
+        }
+        if (p->filter) {
+            for (int d = 0; d < D.ndim; d++) ST(filter_dir(d, p->alpha_f, W(W_PHIS), W(W_PHIS)));
+            ST(bc(W(W_PHIS), poisson));
+        }
+        ProfScope ps(g, WD_K_NORM);
+        CK(launch_norms<T>(D, W(W_PHIS), W(W_PHIN), g->mask, g->partial, g->counter, g->result,
+                           g->nred, st));
+        return WD_OK;
+    }
+
+    wd_status read_norms(double scale, double* l2, double* linf)
+    {
+        CK(cudaMemcpyAsync(g->hres, g->result, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        double n = g->nactive > 0 ? (double)g->nactive : 1.0;
+        *l2 = std::sqrt(g->hres[0] / n) / scale;
+        *linf = g->hres[1] / scale;
+        return WD_OK;
+    }
+
+    wd_status spalding_from_phin()
+    {
+        ST(grad_parts(W(W_PHIN), false));
+        T* U[3] = {W(W_U0), W(W_U1), W(W_U2)};
+        CK(launch_spalding<T, M>(D, U, W(W_PHIN), W(W_PHIN), st));
+        return WD_OK;
+    }
+
+    // full solve; phi_user is read for WD_INIT_GIVEN (or warm) and receives the result
+    wd_status solve(void* phi_user, wd_stats* stats, bool warm)
+    {
+        const double L = g->desc.L_ref;
+        int every = p->check_every > 0 ? p->check_every : 1;
+        wd_stats s;
+        std::memset(&s, 0, sizeof(s));
+        int init = warm ? WD_INIT_GIVEN : p->init;
+        if (init == WD_INIT_GIVEN) {
+            CK(to_padded(g, W(W_PHIN), phi_user, sizeof(T)));
+        } else {
+            CK(launch_fill<T>(W(W_PHIN), D.total, T(0), st));
+        }
+        if (init == WD_INIT_POISSON) {
+            ST(bc(W(W_PHIN), true));
+            int it = 0;
+            double l2 = 0, li = 0;
+            while (it < p->poisson_max_iters) {
+                ST(step(true));
+                it++;
+                if (p->poisson_tol > 0.0 && it % every == 0) {
+                    ST(read_norms(L * L, &l2, &li));
+                    if (!std::isfinite(l2) || !std::isfinite(li)) break;
+                    if (l2 <= p->poisson_tol) break;
+                }
+            }
+            s.poisson_iters = it;
+            ST(spalding_from_phin());
+        }
+        ST(bc(W(W_PHIN), false));
+        int it = 0;
+        double l2 = 0, li = 0;
+        bool have_tol = p->tol_l2 > 0.0 || p->tol_linf > 0.0;
+        bool checked_last = true;
+        wd_status rc = WD_OK;
+        while (it < p->max_iters) {
+            ST(step(false));
+            it++;
+            checked_last = false;
+            if (it % every == 0 || it == p->max_iters) {
+                ST(read_norms(L, &l2, &li));
+                checked_last = true;
+                if (!std::isfinite(l2) || !std::isfinite(li)) {
+                    s.diverged = 1;
+                    rc = WD_ERR_DIVERGED;
+                    break;
+                }
+                if (have_tol && (p->tol_l2 <= 0.0 || l2 <= p->tol_l2) &&
+                    (p->tol_linf <= 0.0 || li <= p->tol_linf)) {
+                    s.converged = 1;
+                    break;
+                }
+            }
+        }
+        if (!checked_last) ST(read_norms(L, &l2, &li));
+        if (rc == WD_OK && have_tol && !s.converged) rc = WD_ERR_NOT_CONVERGED;
+        s.iters = it;
+        s.res_l2 = l2;
+        s.res_linf = li;
+        s.device_bytes = g->bytes;
+        CK(from_padded(g, phi_user, W(W_PHIN), sizeof(T)));
+        CK(cudaStreamSynchronize(st));
+        if (stats) *stats = s;
+        if (rc == WD_ERR_DIVERGED) set_error(rc, "non-finite pseudo-step change");
+        if (rc == WD_ERR_NOT_CONVERGED) set_error(rc, "max_iters reached before the tolerance");
+        return rc;
+    }
+
+    wd_status steps(int kind, void* phi_user, int n, wd_stats* stats)
+    {
+        bool poisson = kind == 1;
+        double scale = poisson ? g->desc.L_ref * g->desc.L_ref : g->desc.L_ref;
+        CK(to_padded(g, W(W_PHIN), phi_user, sizeof(T)));
+        for (int i = 0; i < n; i++) ST(step(poisson));
+        double l2 = 0, li = 0;
+        if (n > 0) ST(read_norms(scale, &l2, &li));
+        CK(from_padded(g, phi_user, W(W_PHIN), sizeof(T)));
+        CK(cudaStreamSynchronize(st));
+        if (stats) {
+            std::memset(stats, 0, sizeof(*stats));
+            if (poisson) stats->poisson_iters = n;
+            else stats->iters = n;
+            stats->res_l2 = l2;
+            stats->res_linf = li;
+            stats->diverged = !(std::isfinite(l2) && std::isfinite(li));
+            stats->device_bytes = g->bytes;
+        }
+        return WD_OK;
+    }
+
+    wd_status rhs(int kind, const void* phi_user, void* R_user, void* dt_user)
+    {
+        bool poisson = kind == 1;
+        CK(to_padded(g, W(W_PHIN), phi_user, sizeof(T)));
+        ST(rhs_into(W(W_PHIN), W(W_PHIS), poisson, -1));
+        if (R_user) CK(from_padded(g, R_user, W(W_PHIS), sizeof(T)));
+        if (dt_user) CK(from_padded(g, dt_user, W(W_DT), sizeof(T)));
+        return WD_OK;
+    }
+};
+
+template <typename F>
+static wd_status dispatch(wd_grid g, F&& fn)
+{
+    switch (g->desc.precision) {
+    case WD_FP64: {
+        auto r = fn((double*)nullptr, (double*)nullptr);
+        return r;
+    }
+    case WD_FP32_METRIC64: return fn((float*)nullptr, (double*)nullptr);
+    default: return fn((float*)nullptr, (float*)nullptr);
+    }
+}
+
+// ------------------------------------------------------------------------------------
+// grid creation
+// ------------------------------------------------------------------------------------
+
+template <typename T, typename M>
+static wd_status create_impl(wd_grid g, const double* xyz_host, const uint8_t* mask_host,
+                             const double* dval_host)
+{
+    const Dims& D = g->D;
+    cudaStream_t st = g->stream;
+    const long long tot = D.total;
+    // coordinates
+    ST(dmalloc(g, (void**)&g->xyz, (size_t)tot * 3 * 8));
+    CK(cudaMemsetAsync(g->xyz, 0, (size_t)tot * 3 * 8, st));
+    for (int m = 0; m < D.ndim; m++)
+        CK(cudaMemcpy2DAsync(g->xyz + m * tot, (size_t)D.pitch * 8,
+                             xyz_host + (size_t)m * D.n[0] * D.n[1] * D.n[2], (size_t)D.n[0] * 8,
+                             (size_t)D.n[0] * 8, (size_t)D.n[1] * D.n[2], cudaMemcpyHostToDevice, st));
+    // line tables
+    for (int d = 0; d < D.ndim; d++) {
+        std::vector<double> a, c;
+        int imp;
+        derivative_rows(g->desc.scheme, D.n[d], D.per[d], a, c, imp);
+        ST(build_line_table(D.n[d], D.per[d], a, c, imp, g->dtab[d]));
+        std::vector<double> z(D.n[d], 0.0);
+        ST(build_line_table(D.n[d], D.per[d], z, z, 0, g->etab[d]));
+    }
+    // metrics: A[(m*3+l)] = dx_m/dxi_l by the grid's scheme, periodic shift added back
+    ST(dmalloc(g, (void**)&g->xi_d, (size_t)tot * 9 * 8));
+    ST(dmalloc(g, (void**)&g->J_d, (size_t)tot * 8));
+    ST(dmalloc(g, (void**)&g->dx_d, (size_t)tot * 3 * 8));
+    CK(cudaMemsetAsync(g->xi_d, 0, (size_t)tot * 9 * 8, st));
+    CK(cudaMemsetAsync(g->dx_d, 0, (size_t)tot * 3 * 8, st));
+    if (sizeof(M) == 8) {
+        g->xi_m = g->xi_d;
+        g->xi_alias = 1;
+    } else {
+        ST(dmalloc(g, &g->xi_m, (size_t)tot * 9 * sizeof(M)));
+        CK(cudaMemsetAsync(g->xi_m, 0, (size_t)tot * 9 * sizeof(M), st));
+        g->xi_alias = 0;
+    }
+    ST(dmalloc(g, &g->sig1, (size_t)tot * sizeof(M)));
+    ST(dmalloc(g, &g->sig2, (size_t)tot * sizeof(M)));
+    ST(dmalloc(g, &g->lads, (size_t)tot * 3 * sizeof(M)));
+    {
+        double* A = nullptr;
+        double* tmp = nullptr;
+        if (cudaMalloc(&A, (size_t)tot * 9 * 8) != cudaSuccess || cudaMalloc(&tmp, (size_t)tot * 8) != cudaSuccess) {
+            cudaFree(A);
+            cudaGetLastError();
+            return set_error(WD_ERR_OOM, "metric scratch");
+        }
+        cudaError_t ce = cudaSuccess;
+        LineOp op;
+        std::memset(&op, 0, sizeof(op));
+        op.kind = OPK_DERIV;
+        op.scheme = g->desc.scheme;
+        for (int l = 0; l < D.ndim && ce == cudaSuccess; l++)
+            for (int m = 0; m < D.ndim && ce == cudaSuccess; m++) {
+                double shift = D.per[l] ? g->desc.period[l][m] : 0.0;
+                const double* src = g->xyz + m * tot;
+                if (shift != 0.0) {
+                    ce = launch_unwrap(D, l, src, shift, tmp, st);
+                    src = tmp;
+                }
+                Fields<double> f;
+                std::memset(&f, 0, sizeof(f));
+                f.in[0] = src;
+                f.out[0] = A + (long long)(m * 3 + l) * tot;
+                if (ce == cudaSuccess)
+                    ce = launch_line<double, double>(D, l, g->dtab[l], op, 1, 0, f, nullptr, 0, 0, st);
+                // derivative of the removed linear part shift * t / n: shift / n, exact for
+                // every scheme
+                if (ce == cudaSuccess && shift != 0.0)
+                    ce = launch_add_const(D, A + (long long)(m * 3 + l) * tot, shift / D.n[l], st);
+            }
+        if (ce != cudaSuccess) {
+            cudaFree(A);
+            cudaFree(tmp);
+            return cuda_error(ce, "metric derivatives");
+        }
+        cudaFree(tmp);
+        ce = launch_metric_finish<M>(D, A, g->xi_d, g->J_d, g->dx_d,
+                                     g->xi_alias ? nullptr : (M*)g->xi_m, (M*)g->sig1, (M*)g->sig2, st);
+        cudaStreamSynchronize(st);
+        cudaFree(A);
+        if (ce != cudaSuccess) return cuda_error(ce, "metric finish");
+    }
+    // far-field spacing ratios
+    long long fmax = 0;
+    for (int d = 0; d < 3; d++) {
+        long long f = (long long)D.n[(d + 1) % 3] * D.n[(d + 2) % 3];
+        if (f > fmax) fmax = f;
+    }
+    g->fmax = fmax;
+    ST(dmalloc(g, (void**)&g->ffr, (size_t)fmax * 6 * 8));
+    CK(cudaMemsetAsync(g->ffr, 0, (size_t)fmax * 6 * 8, st));
+    CK(launch_ff_ratio(D, g->xyz, g->ffr, fmax, st));
+    // Dirichlet set: wall faces + caller mask
+    ST(dmalloc(g, (void**)&g->wall, (size_t)tot));
+    ST(dmalloc(g, (void**)&g->mask, (size_t)tot));
+    ST(dmalloc(g, &g->dval, (size_t)tot * sizeof(T)));
+    {
+        std::vector<uint8_t> wall((size_t)tot, 0);
+        for (int k = 0; k < D.n[2]; k++)
+            for (int j = 0; j < D.n[1]; j++)
+                for (int i = 0; i < D.n[0]; i++) {
+                    int c[3] = {i, j, k};
+                    bool w = false;
+                    for (int d = 0; d < D.ndim; d++) {
+                        if (c[d] == 0 && g->desc.bc_lo[d] == WD_BC_WALL) w = true;
+                        if (c[d] == D.n[d] - 1 && g->desc.bc_hi[d] == WD_BC_WALL) w = true;
+                    }
+                    wall[(size_t)D.idx(i, j, k)] = w;
+                }
+        CK(cudaMemcpyAsync(g->wall, wall.data(), (size_t)tot, cudaMemcpyHostToDevice, st));
+        CK(cudaStreamSynchronize(st));
+    }
+    {
+        uint8_t* um = nullptr;
+        T* uv = nullptr;
+        size_t Nd = (size_t)D.n[0] * D.n[1] * D.n[2];
+        if (mask_host) {
+            if (cudaMalloc(&um, Nd) != cudaSuccess) return set_error(WD_ERR_OOM, "mask upload");
+            cudaMemcpy(um, mask_host, Nd, cudaMemcpyHostToDevice);
+            if (dval_host) {
+                std::vector<T> v(Nd);
+                for (size_t q = 0; q < Nd; q++) v[q] = (T)dval_host[q];
+                if (cudaMalloc(&uv, Nd * sizeof(T)) != cudaSuccess) {
+                    cudaFree(um);
+                    return set_error(WD_ERR_OOM, "dval upload");
+                }
+                cudaMemcpy(uv, v.data(), Nd * sizeof(T), cudaMemcpyHostToDevice);
+            }
+        }
+        cudaError_t ce = launch_mask_merge<T>(D, um, uv, g->mask, (T*)g->dval, g->wall, st);
+        cudaStreamSynchronize(st);
+        cudaFree(um);
+        cudaFree(uv);
+        if (ce != cudaSuccess) return cuda_error(ce, "mask merge");
+    }
+    ST(dmalloc(g, (void**)&g->dcount, sizeof(unsigned long long)));
+    // work arrays, reduction buffers
+    for (int k = 0; k < W_NWORK; k++) {
+        ST(dmalloc(g, &g->w[k], (size_t)tot * sizeof(T)));
+        CK(cudaMemsetAsync(g->w[k], 0, (size_t)tot * sizeof(T), st));
+    }
+    g->nred = (int)std::min<long long>((tot + 255) / 256, 1024);
+    ST(dmalloc(g, (void**)&g->partial, (size_t)g->nred * 2 * 8));
+    ST(dmalloc(g, (void**)&g->counter, sizeof(unsigned)));
+    ST(dmalloc(g, (void**)&g->result, 2 * 8));
+    CK(cudaMemsetAsync(g->counter, 0, sizeof(unsigned), st));
+    CK(cudaMemsetAsync(g->result, 0, 2 * 8, st));
+    if (cudaMallocHost(&g->hres, 2 * sizeof(double)) != cudaSuccess) return set_error(WD_ERR_OOM, "pinned");
+    CK(cudaStreamSynchronize(st));
+    return WD_OK;
+}
+
+static wd_status count_active(wd_grid g)
+{
+    CK(cudaMemsetAsync(g->dcount, 0, sizeof(unsigned long long), g->stream));
+    CK(launch_count(g->D, g->mask, g->dcount, g->stream));
+    unsigned long long c = 0;
+    CK(cudaMemcpyAsync(&c, g->dcount, sizeof(c), cudaMemcpyDeviceToHost, g->stream));
+    CK(cudaStreamSynchronize(g->stream));
+    g->nactive = (long long)c;
+    return WD_OK;
+}
+
+extern "C" {
+
+void wd_default_params(int scheme, wd_solve_params* p)
+{
+    if (!p) return;
+    std::memset(p, 0, sizeof(*p));
+    p->equation = WD_HJ_LAD;
+    p->curvature = 0;
+    p->eps = 0.2;
+    p->C_lad = 0.1;
+    p->lad_exp = 3.0;
+    p->alpha_f = 0.49;
+    p->filter = 1;
+    p->cfl = (scheme == WD_C4 || scheme == WD_C6) ? 0.6 : 0.8;
+    p->eps0 = 1e-8;
+    p->tol_l2 = 1e-10;
+    p->tol_linf = 0.0;
+    p->max_iters = 20000;
+    p->check_every = 10;
+    p->init = WD_INIT_POISSON;
+    p->poisson_tol = 0.0;
+    p->poisson_max_iters = 100;
+}
+
+wd_status wd_create_grid(const wd_grid_desc* desc, const double* xyz_host, const uint8_t* mask_host,
+                         const double* dval_host, void* cuda_stream, wd_grid* out)
+{
+    if (!out) return set_error(WD_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    ST(validate_desc(desc));
+    if (!xyz_host) return set_error(WD_ERR_INVALID_ARG, "xyz_host is NULL");
+    wd_grid g = new wd_grid_s();
+    g->desc = *desc;
+    g->stream = (cudaStream_t)cuda_stream;
+    g->es = desc->precision == WD_FP64 ? 8 : 4;
+    Dims& D = g->D;
+    D.ndim = desc->ndim;
+    for (int k = 0; k < 3; k++) {
+        D.n[k] = desc->n[k];
+        D.per[k] = k < desc->ndim && desc->bc_lo[k] == WD_BC_PERIODIC;
+    }
+    D.pitch = (desc->n[0] + 31) / 32 * 32;
+    D.total = (long long)D.pitch * D.n[1] * D.n[2];
+    wd_status s = dispatch(g, [&](auto* t, auto* m) {
+        using T = std::remove_pointer_t<decltype(t)>;
+        using M = std::remove_pointer_t<decltype(m)>;
+        return create_impl<T, M>(g, xyz_host, mask_host, dval_host);
+    });
+    if (s == WD_OK) s = count_active(g);
+    if (s != WD_OK) {
+        std::string keep = g_err;
+        release(g);
+        g_err = keep;
+        return s;
+    }
+    *out = g;
+    return WD_OK;
+}
+
+void wd_destroy_grid(wd_grid g)
+{
+    if (!g) return;
+    cudaStreamSynchronize(g->stream);
+    release(g);
+}
+
+wd_status wd_set_stream(wd_grid g, void* cuda_stream)
+{
+    if (!g) return set_error(WD_ERR_INVALID_ARG, "grid is NULL");
+    g->stream = (cudaStream_t)cuda_stream;
+    return WD_OK;
+}
+
+static wd_status check_params(const wd_solve_params* p)
+{
+    if (!p) return set_error(WD_ERR_INVALID_ARG, "params is NULL");
+    if (p->equation < 0 || p->equation > 2) return set_error(WD_ERR_INVALID_ARG, "bad equation");
+    if (!(std::fabs(p->alpha_f) < 0.5)) return set_error(WD_ERR_INVALID_ARG, "|alpha_f| must be < 0.5");
+    if (!(p->cfl > 0.0)) return set_error(WD_ERR_INVALID_ARG, "cfl must be positive");
+    if (p->max_iters < 0 || p->poisson_max_iters < 0) return set_error(WD_ERR_INVALID_ARG, "negative iteration count");
+    if (p->init < 0 || p->init > 2) return set_error(WD_ERR_INVALID_ARG, "bad init");
+    return WD_OK;
+}
+
+wd_status wd_solve(wd_grid g, const wd_solve_params* p, void* phi_dev, wd_stats* stats)
+{
+    if (!g || !phi_dev) return set_error(WD_ERR_INVALID_ARG, "NULL grid or phi");
+    ST(check_params(p));
+    auto t0 = std::chrono::steady_clock::now();
+    wd_status s = dispatch(g, [&](auto* t, auto* m) {
+        using T = std::remove_pointer_t<decltype(t)>;
+        using M = std::remove_pointer_t<decltype(m)>;
+        Solver<T, M> S(g, p);
+        return S.solve(phi_dev, stats, false);
+    });
+    if (stats)
+        stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    return s;
+}
+
+wd_status wd_step_unsteady(wd_grid g, const uint8_t* mask_dev, const void* dval_dev,
+                           const wd_solve_params* p, void* phi_dev, wd_stats* stats)
+{
+    if (!g || !phi_dev) return set_error(WD_ERR_INVALID_ARG, "NULL grid or phi");
+    ST(check_params(p));
+    auto t0 = std::chrono::steady_clock::now();
+    wd_status s = dispatch(g, [&](auto* t, auto* m) {
+        using T = std::remove_pointer_t<decltype(t)>;
+        using M = std::remove_pointer_t<decltype(m)>;
+        if (mask_dev) {
+            CK(launch_mask_merge<T>(g->D, mask_dev, (const T*)dval_dev, g->mask, (T*)g->dval, g->wall,
+                                    g->stream));
+            ST(count_active(g));
+        }
+        Solver<T, M> S(g, p);
+        return S.solve(phi_dev, stats, true);
+    });
+    if (stats)
+        stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    return s;
+}
+
+wd_status wd_solve_batch(wd_grid* grids, int n, const wd_solve_params* p, void** phi_dev,
+                         wd_stats* stats)
+{
+    if (!grids || !phi_dev || n < 0) return set_error(WD_ERR_INVALID_ARG, "bad batch");
+    wd_status first = WD_OK;
+    for (int i = 0; i < n; i++) {
+        wd_status s = wd_solve(grids[i], p, phi_dev[i], stats ? stats + i : nullptr);
+        if (s != WD_OK && first == WD_OK) first = s;
+    }
+    return first;
+}
+
+size_t wd_query_footprint(const wd_grid_desc* desc, const wd_solve_params* p)
+{
+    (void)p;
+    if (validate_desc(desc) != WD_OK) return 0;
+    return footprint_bytes(desc);
+}
+
+const char* wd_status_string(wd_status s)
+{
+    switch (s) {
+    case WD_OK: return "ok";
+    case WD_ERR_INVALID_ARG: return "invalid argument";
+    case WD_ERR_OOM: return "out of device memory";
+    case WD_ERR_CUDA: return "CUDA error";
+    case WD_ERR_NOT_CONVERGED: return "not converged";
+    case WD_ERR_DIVERGED: return "diverged";
+    case WD_ERR_TIMEOUT: return "timeout";
+    default: return "unknown status";
+    }
+}
+
+const char* wd_last_error(void) { return g_err.c_str(); }
+
+wd_status wd_get_metrics(wd_grid g, double* xi_dev, double* J_dev, double* dx_dev)
+{
+    if (!g) return set_error(WD_ERR_INVALID_ARG, "grid is NULL");
+    long long tot = g->D.total;
+    size_t N = (size_t)g->D.n[0] * g->D.n[1] * g->D.n[2];
+    for (int k = 0; k < 9 && xi_dev; k++) CK(from_padded(g, xi_dev + k * N, g->xi_d + k * tot, 8));
+    if (J_dev) CK(from_padded(g, J_dev, g->J_d, 8));
+    for (int k = 0; k < 3 && dx_dev; k++) CK(from_padded(g, dx_dev + k * N, g->dx_d + k * tot, 8));
+    return WD_OK;
+}
+
+wd_status wd_derivative(wd_grid g, int dir, const void* in_dev, void* out_dev)
+{
+    if (!g || !in_dev || !out_dev || dir < 0 || dir >= g->desc.ndim)
+        return set_error(WD_ERR_INVALID_ARG, "bad derivative arguments");
+    return dispatch(g, [&](auto* t, auto* m) {
+        using T = std::remove_pointer_t<decltype(t)>;
+        using M = std::remove_pointer_t<decltype(m)>;
+        Solver<T, M> S(g, nullptr);
+        CK(to_padded(g, g->w[W_T0], in_dev, sizeof(T)));
+        ST(S.deriv_dir(dir, (const T*)g->w[W_T0], (T*)g->w[W_T1]));
+        CK(from_padded(g, out_dev, g->w[W_T1], sizeof(T)));
+        return WD_OK;
+    });
+}
+
+wd_status wd_filter(wd_grid g, double alpha_f, int dir, const void* in_dev, void* out_dev)
+{
+    if (!g || !in_dev || !out_dev || dir < 0 || dir >= g->desc.ndim || !(std::fabs(alpha_f) < 0.5))
+        return set_error(WD_ERR_INVALID_ARG, "bad filter arguments");
+    return dispatch(g, [&](auto* t, auto* m) {
+        using T = std::remove_pointer_t<decltype(t)>;
+        using M = std::remove_pointer_t<decltype(m)>;
+        Solver<T, M> S(g, nullptr);
+        CK(to_padded(g, g->w[W_T0], in_dev, sizeof(T)));
+        ST(S.filter_dir(dir, alpha_f, (const T*)g->w[W_T0], (T*)g->w[W_T0]));
+        CK(from_padded(g, out_dev, g->w[W_T0], sizeof(T)));
+        return WD_OK;
+    });
+}
+
+wd_status wd_rhs(wd_grid g, const wd_solve_params* p, int kind, const void* phi_dev, void* R_dev,
+                 void* dt_dev)
+{
+    if (!g || !phi_dev || (kind != 0 && kind != 1)) return set_error(WD_ERR_INVALID_ARG, "bad rhs arguments");
+    ST(check_params(p));
+    return dispatch(g, [&](auto* t, auto* m) {
+        using T = std::remove_pointer_t<decltype(t)>;
+        using M = std::remove_pointer_t<decltype(m)>;
+        Solver<T, M> S(g, p);
+        return S.rhs(kind, phi_dev, R_dev, dt_dev);
+    });
+}
+
+wd_status wd_spalding(wd_grid g, const void* phip_dev, void* phi_dev)
+{
+    if (!g || !phip_dev || !phi_dev) return set_error(WD_ERR_INVALID_ARG, "bad spalding arguments");
+    return dispatch(g, [&](auto* t, auto* m) {
+        using T = std::remove_pointer_t<decltype(t)>;
+        using M = std::remove_pointer_t<decltype(m)>;
+        Solver<T, M> S(g, nullptr);
+        CK(to_padded(g, g->w[W_PHIN], phip_dev, sizeof(T)));
+        ST(S.spalding_from_phin());
+        CK(from_padded(g, phi_dev, g->w[W_PHIN], sizeof(T)));
+        return WD_OK;
+    });
+}
+
+wd_status wd_apply_bc(wd_grid g, void* phi_dev)
+{
+    if (!g || !phi_dev) return set_error(WD_ERR_INVALID_ARG, "bad bc arguments");
+    return dispatch(g, [&](auto* t, auto* m) {
+        using T = std::remove_pointer_t<decltype(t)>;
+        using M = std::remove_pointer_t<decltype(m)>;
+        Solver<T, M> S(g, nullptr);
+        CK(to_padded(g, g->w[W_PHIN], phi_dev, sizeof(T)));
+        ST(S.bc((T*)g->w[W_PHIN], false));
+        CK(from_padded(g, phi_dev, g->w[W_PHIN], sizeof(T)));
+        return WD_OK;
+    });
+}
+
+wd_status wd_steps(wd_grid g, const wd_solve_params* p, int kind, void* phi_dev, int nsteps,
+                   wd_stats* stats)
+{
+    if (!g || !phi_dev || (kind != 0 && kind != 1) || nsteps < 0)
+        return set_error(WD_ERR_INVALID_ARG, "bad steps arguments");
+    ST(check_params(p));
+    return dispatch(g, [&](auto* t, auto* m) {
+        using T = std::remove_pointer_t<decltype(t)>;
+        using M = std::remove_pointer_t<decltype(m)>;
+        Solver<T, M> S(g, p);
+        return S.steps(kind, phi_dev, nsteps, stats);
+    });
+}
+
+wd_status wd_profile(wd_grid g, int enable)
+{
+    if (!g) return set_error(WD_ERR_INVALID_ARG, "grid is NULL");
+    if (enable) {
+        CK(prof_flush(g));
+        for (int k = 0; k < WD_K_NCLASS; k++) {
+            g->prof_ms[k] = 0.0;
+            g->prof_n[k] = 0;
+        }
+    }
+    g->prof_on = enable != 0;
+    return WD_OK;
+}
+
+wd_status wd_profile_read(wd_grid g, int cls, double* ms_total, long long* launches)
+{
+    if (!g || cls < 0 || cls >= WD_K_NCLASS) return set_error(WD_ERR_INVALID_ARG, "bad profile query");
+    CK(prof_flush(g));
+    if (ms_total) *ms_total = g->prof_ms[cls];
+    if (launches) *launches = g->prof_n[cls];
+    return WD_OK;
+}
+
+}  // extern "C"

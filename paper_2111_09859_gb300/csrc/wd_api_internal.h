@@ -1,0 +1,91 @@
+// wd_api_internal.h -- host-side declarations shared by the libwd translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "wd.h"
+#include "wd_internal.cuh"
+
+namespace wd {
+
+wd_status set_error(wd_status s, const char* msg);
+wd_status cuda_error(cudaError_t e, const char* where);
+
+bool dense_solve(int n, std::vector<double>& M, std::vector<double>& r);
+bool filter_coefficients(int hw, double al, double* a);
+void derivative_rows(int scheme, int N, int periodic, std::vector<double>& a,
+                     std::vector<double>& c, int& implicit);
+void filter_rows(double al, int N, int periodic, std::vector<double>& a, std::vector<double>& c,
+                 int& implicit);
+int choose_chunks(int N);
+wd_status build_line_table(int N, int periodic, const std::vector<double>& a,
+                           const std::vector<double>& c, int implicit, HostLineTab& tab);
+void free_line_table(HostLineTab& tab);
+
+// arguments of the pointwise stage kernel (right-hand side + RK4 stage update)
+template <typename T, typename M>
+struct StageArgs {
+    const T* src;        // phi at which R is evaluated
+    T* dst;              // stage output (RK modes) or R (rhs-only mode)
+    const T* phin;       // state at the start of the pseudo step
+    T* acc;              // running sum of the RK4 weights times R
+    T* dt;               // local pseudo time step
+    const T* U[3];       // grad(phi), physical components
+    const T* lap;        // div(U)
+    const T* kap;        // div(n) (curvature only)
+    const T* lad;        // smoothed C|LAD| (LAD only)
+    const M* sig1;       // sum_l |grad xi_l|
+    const M* sig2;       // sum_l |grad xi_l|^2
+    double eps, cfl;
+    int equation, curvature, poisson;
+};
+
+// stage codes for launch_stage: 0..3 = RK4 stages, -1 = right-hand side and dt only
+template <typename T, typename M>
+cudaError_t launch_line(const Dims& D, int dir, const HostLineTab& tab, const LineOp& op, int nf,
+                        int epi, const Fields<T>& f, const M* xi, int nU, int accumulate,
+                        cudaStream_t st);
+template <typename T, typename M>
+cudaError_t launch_grad(const Dims& D, const T* const* Dl, const M* xi, T* const* U,
+                        T* const* nv, double eps0, cudaStream_t st);
+template <typename T, typename M>
+cudaError_t launch_lad_raw(const Dims& D, const T* phi, const M* lads, double C, T* out,
+                           cudaStream_t st);
+template <typename T, typename M>
+cudaError_t launch_stage(const Dims& D, const StageArgs<T, M>& a, int stage, cudaStream_t st);
+template <typename T, typename M>
+cudaError_t launch_spalding(const Dims& D, const T* const* U, const T* phip, T* phi,
+                            cudaStream_t st);
+template <typename T>
+cudaError_t launch_bc_face(const Dims& D, int dir, int kind_lo, int kind_hi, const double* rlo,
+                           const double* rhi, T* phi, cudaStream_t st);
+template <typename T>
+cudaError_t launch_bc_mask(const Dims& D, const uint8_t* mask, const T* dval, T* phi,
+                           cudaStream_t st);
+template <typename T>
+cudaError_t launch_norms(const Dims& D, const T* newp, T* oldp, const uint8_t* mask,
+                         double* partial, unsigned* counter, double* result, int nblocks,
+                         cudaStream_t st);
+template <typename T>
+cudaError_t launch_fill(T* p, long long n, T v, cudaStream_t st);
+
+cudaError_t launch_unwrap(const Dims& D, int dir, const double* x, double shift, double* out,
+                          cudaStream_t st);
+cudaError_t launch_add_const(const Dims& D, double* p, double c, cudaStream_t st);
+template <typename M>
+cudaError_t launch_metric_finish(const Dims& D, const double* A, double* xi_d, double* J,
+                                 double* dx, M* xi_m, M* sig1, M* sig2, cudaStream_t st);
+template <typename M>
+cudaError_t launch_lad_scale(const Dims& D, const double* xi_d, const double* dx, double ex,
+                             M* lads, cudaStream_t st);
+cudaError_t launch_ff_ratio(const Dims& D, const double* xyz, double* ratio, long long fmax,
+                            cudaStream_t st);
+template <typename T>
+cudaError_t launch_mask_merge(const Dims& D, const uint8_t* src_dense, const T* val_dense,
+                              uint8_t* mask, T* dval, const uint8_t* wallmask, cudaStream_t st);
+cudaError_t launch_count(const Dims& D, const uint8_t* mask, unsigned long long* out,
+                         cudaStream_t st);
+
+}  // namespace wd

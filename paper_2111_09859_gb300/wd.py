@@ -1,0 +1,311 @@
+"""Thin ctypes binding of libwd (include/wd.h).
+
+Argument marshalling only: every step of the method runs in the CUDA kernels of libwd.
+PyTorch supplies device memory (tensors) and the current CUDA stream.  There is no CPU
+fallback: if the compiled library is missing, loading fails with an error that says how
+to build it.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_lib", "libwd.so")
+
+OK, ERR_INVALID_ARG, ERR_OOM, ERR_CUDA, ERR_NOT_CONVERGED, ERR_DIVERGED, ERR_TIMEOUT = range(7)
+BC_WALL, BC_FARFIELD, BC_NEUMANN, BC_PERIODIC = 0, 1, 2, 3
+FP64, FP32_METRIC64, FP32 = 0, 1, 2
+HJ_STD, HJ_LAD, EIKONAL = 0, 1, 2
+E2, E4, E6, C4, C6 = 0, 1, 2, 3, 4
+INIT_ZERO, INIT_POISSON, INIT_GIVEN = 0, 1, 2
+
+
+class WDError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"libwd status {status}: {msg}")
+        self.status = status
+
+
+class GridDesc(C.Structure):
+    _fields_ = [
+        ("ndim", C.c_int), ("n", C.c_int * 3), ("bc_lo", C.c_int * 3), ("bc_hi", C.c_int * 3),
+        ("period", (C.c_double * 3) * 3), ("precision", C.c_int), ("scheme", C.c_int),
+        ("L_ref", C.c_double),
+    ]
+
+
+class SolveParams(C.Structure):
+    _fields_ = [
+        ("equation", C.c_int), ("curvature", C.c_int), ("eps", C.c_double), ("C_lad", C.c_double),
+        ("lad_exp", C.c_double), ("alpha_f", C.c_double), ("filter", C.c_int), ("cfl", C.c_double),
+        ("eps0", C.c_double), ("tol_l2", C.c_double), ("tol_linf", C.c_double),
+        ("max_iters", C.c_int), ("check_every", C.c_int), ("init", C.c_int),
+        ("poisson_tol", C.c_double), ("poisson_max_iters", C.c_int),
+    ]
+
+
+class Stats(C.Structure):
+    _fields_ = [
+        ("iters", C.c_int), ("poisson_iters", C.c_int), ("res_l2", C.c_double),
+        ("res_linf", C.c_double), ("converged", C.c_int), ("diverged", C.c_int),
+        ("seconds", C.c_double), ("device_bytes", C.c_size_t),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lock = threading.Lock()
+_lib = None
+
+# name -> (restype, argtypes); mirrors include/wd.h
+_vp, _i, _d = C.c_void_p, C.c_int, C.c_double
+SIGNATURES = {
+    "wd_default_params": (None, [_i, C.POINTER(SolveParams)]),
+    "wd_create_grid": (_i, [C.POINTER(GridDesc), _vp, _vp, _vp, _vp, C.POINTER(_vp)]),
+    "wd_destroy_grid": (None, [_vp]),
+    "wd_set_stream": (_i, [_vp, _vp]),
+    "wd_solve": (_i, [_vp, C.POINTER(SolveParams), _vp, C.POINTER(Stats)]),
+    "wd_step_unsteady": (_i, [_vp, _vp, _vp, C.POINTER(SolveParams), _vp, C.POINTER(Stats)]),
+    "wd_solve_batch": (_i, [C.POINTER(_vp), _i, C.POINTER(SolveParams), C.POINTER(_vp), C.POINTER(Stats)]),
+    "wd_query_footprint": (C.c_size_t, [C.POINTER(GridDesc), C.POINTER(SolveParams)]),
+    "wd_status_string": (C.c_char_p, [_i]),
+    "wd_last_error": (C.c_char_p, []),
+    "wd_get_metrics": (_i, [_vp, _vp, _vp, _vp]),
+    "wd_derivative": (_i, [_vp, _i, _vp, _vp]),
+    "wd_filter": (_i, [_vp, _d, _i, _vp, _vp]),
+    "wd_rhs": (_i, [_vp, C.POINTER(SolveParams), _i, _vp, _vp, _vp]),
+    "wd_spalding": (_i, [_vp, _vp, _vp]),
+    "wd_apply_bc": (_i, [_vp, _vp]),
+    "wd_steps": (_i, [_vp, C.POINTER(SolveParams), _i, _vp, _i, C.POINTER(Stats)]),
+    "wd_profile": (_i, [_vp, _i]),
+    "wd_profile_read": (_i, [_vp, _i, C.POINTER(C.c_double), C.POINTER(C.c_longlong)]),
+}
+
+K_DERIV, K_DIV, K_FILTER, K_GAUSS, K_POINT, K_BC, K_NORM = range(7)
+K_NAMES = ("deriv", "div", "filter", "gauss", "point", "bc", "norm")
+
+
+def lib(path: str | None = None):
+    """Loads libwd.so (built by paper_2111_09859_gb300.build / __graft_entry__.build())."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            p = path or LIB_PATH
+            if not os.path.exists(p):
+                raise ImportError(
+                    f"libwd.so not found at {p}: build it with "
+                    "`python -c 'import __graft_entry__ as g; g.build()'`")
+            L = C.CDLL(p)
+            for name, (res, args) in SIGNATURES.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+def _check(status):
+    if status != OK:
+        msg = lib().wd_last_error().decode(errors="replace")
+        raise WDError(status, msg)
+
+
+def default_params(scheme: int, **overrides) -> SolveParams:
+    p = SolveParams()
+    lib().wd_default_params(scheme, C.byref(p))
+    for k, v in overrides.items():
+        if not hasattr(p, k):
+            raise KeyError(f"unknown solve parameter {k!r}")
+        setattr(p, k, v)
+    return p
+
+
+def _stream_handle(stream=None):
+    import torch
+
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr()) if t is not None else None
+
+
+class Grid:
+    """A structured grid on the GPU (wd_create_grid).
+
+    ``spec`` needs: ``shape`` (ni, nj[, nk]), ``xyz`` (ndim, N) float64 coordinates,
+    ``bc_lo`` / ``bc_hi``, ``period``, ``L_ref``, optional ``mask`` / ``dval``."""
+
+    def __init__(self, spec, precision=FP64, scheme=E4, stream=None):
+        import torch
+
+        self.shape = tuple(int(s) for s in spec.shape)
+        self.ndim = len(self.shape)
+        n = list(self.shape) + [1] * (3 - self.ndim)
+        self.n = n
+        self.N = n[0] * n[1] * n[2]
+        self.precision = precision
+        self.scheme = scheme
+        self.dtype = torch.float64 if precision == FP64 else torch.float32
+        d = GridDesc()
+        d.ndim = self.ndim
+        for k in range(3):
+            d.n[k] = n[k]
+            d.bc_lo[k] = spec.bc_lo[k] if k < self.ndim else BC_WALL
+            d.bc_hi[k] = spec.bc_hi[k] if k < self.ndim else BC_WALL
+            for m in range(3):
+                d.period[k][m] = float(spec.period[k][m]) if spec.period is not None else 0.0
+        d.precision = precision
+        d.scheme = scheme
+        d.L_ref = float(getattr(spec, "L_ref", 1.0))
+        self.desc = d
+        xyz = np.ascontiguousarray(np.asarray(spec.xyz, dtype=np.float64).reshape(self.ndim, -1))
+        mask = getattr(spec, "mask", None)
+        dval = getattr(spec, "dval", None)
+        mask = None if mask is None else np.ascontiguousarray(mask, dtype=np.uint8).reshape(-1)
+        dval = None if dval is None else np.ascontiguousarray(dval, dtype=np.float64).reshape(-1)
+        self.stream = stream
+        h = C.c_void_p()
+        _check(lib().wd_create_grid(
+            C.byref(d), xyz.ctypes.data,
+            None if mask is None else mask.ctypes.data,
+            None if dval is None else dval.ctypes.data,
+            _stream_handle(stream), C.byref(h)))
+        self._h = h
+        self._device = torch.device("cuda", torch.cuda.current_device())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().wd_destroy_grid(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _sync_stream(self):
+        lib().wd_set_stream(self._h, _stream_handle(self.stream))
+
+    def empty(self):
+        import torch
+
+        return torch.empty(self.N, dtype=self.dtype, device=self._device)
+
+    def as_field(self, a):
+        import torch
+
+        t = torch.as_tensor(np.asarray(a).reshape(-1), dtype=self.dtype)
+        return t.to(self._device).contiguous()
+
+    # ---- method ------------------------------------------------------------------------
+    def solve(self, params: SolveParams, phi=None, allow_fail=False):
+        """Steady solve; returns (phi tensor, stats dict)."""
+        phi = self.empty() if phi is None else phi
+        st = Stats()
+        self._sync_stream()
+        s = lib().wd_solve(self._h, C.byref(params), _ptr(phi), C.byref(st))
+        if not allow_fail and s not in (OK, ERR_NOT_CONVERGED):
+            _check(s)
+        d = st.as_dict()
+        d["status"] = s
+        return phi, d
+
+    def step_unsteady(self, params, phi, mask=None, dval=None):
+        st = Stats()
+        self._sync_stream()
+        s = lib().wd_step_unsteady(self._h, _ptr(mask), _ptr(dval), C.byref(params), _ptr(phi),
+                                   C.byref(st))
+        if s not in (OK, ERR_NOT_CONVERGED):
+            _check(s)
+        d = st.as_dict()
+        d["status"] = s
+        return phi, d
+
+    def steps(self, params, phi, n, kind=0):
+        st = Stats()
+        self._sync_stream()
+        _check(lib().wd_steps(self._h, C.byref(params), kind, _ptr(phi), int(n), C.byref(st)))
+        return phi, st.as_dict()
+
+    def rhs(self, params, phi, kind=0):
+        R, dt = self.empty(), self.empty()
+        self._sync_stream()
+        _check(lib().wd_rhs(self._h, C.byref(params), kind, _ptr(phi), _ptr(R), _ptr(dt)))
+        return R, dt
+
+    def derivative(self, f, dir):
+        out = self.empty()
+        self._sync_stream()
+        _check(lib().wd_derivative(self._h, int(dir), _ptr(f), _ptr(out)))
+        return out
+
+    def filter(self, f, dir, alpha_f):
+        out = self.empty()
+        self._sync_stream()
+        _check(lib().wd_filter(self._h, float(alpha_f), int(dir), _ptr(f), _ptr(out)))
+        return out
+
+    def spalding(self, phip):
+        out = self.empty()
+        self._sync_stream()
+        _check(lib().wd_spalding(self._h, _ptr(phip), _ptr(out)))
+        return out
+
+    def apply_bc(self, phi):
+        self._sync_stream()
+        _check(lib().wd_apply_bc(self._h, _ptr(phi)))
+        return phi
+
+    def profile(self, enable=True):
+        _check(lib().wd_profile(self._h, int(bool(enable))))
+
+    def profile_read(self):
+        out = {}
+        for k, name in enumerate(K_NAMES):
+            ms, n = C.c_double(), C.c_longlong()
+            _check(lib().wd_profile_read(self._h, k, C.byref(ms), C.byref(n)))
+            out[name] = (ms.value, n.value)
+        return out
+
+    def metrics(self):
+        import torch
+
+        xi = torch.zeros(9 * self.N, dtype=torch.float64, device=self._device)
+        J = torch.zeros(self.N, dtype=torch.float64, device=self._device)
+        dx = torch.zeros(3 * self.N, dtype=torch.float64, device=self._device)
+        self._sync_stream()
+        _check(lib().wd_get_metrics(self._h, _ptr(xi), _ptr(J), _ptr(dx)))
+        return xi.view(3, 3, self.N), J, dx.view(3, self.N)
+
+
+def solve_batch(grids, params, phis):
+    n = len(grids)
+    hs = (C.c_void_p * n)(*[g._h for g in grids])
+    ps = (C.c_void_p * n)(*[p.data_ptr() for p in phis])
+    sts = (Stats * n)()
+    for g in grids:
+        g._sync_stream()
+    s = lib().wd_solve_batch(hs, n, C.byref(params), ps, sts)
+    return s, [st.as_dict() for st in sts]
+
+
+def footprint(spec, precision=FP64, scheme=E4):
+    d = GridDesc()
+    shape = tuple(spec.shape)
+    d.ndim = len(shape)
+    for k in range(3):
+        d.n[k] = shape[k] if k < len(shape) else 1
+        d.bc_lo[k] = spec.bc_lo[k] if k < len(shape) else BC_WALL
+        d.bc_hi[k] = spec.bc_hi[k] if k < len(shape) else BC_WALL
+    d.precision = precision
+    d.scheme = scheme
+    d.L_ref = 1.0
+    return lib().wd_query_footprint(C.byref(d), None)

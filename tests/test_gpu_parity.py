@@ -1,0 +1,220 @@
+"""GPU parity: every step of the method on the GPU (through the C ABI) against the FP64
+oracle on identical seeded inputs, at sizes the oracle finishes in seconds that still
+span several line chunks, shared-memory tiles and ragged tails.
+
+Tolerances (written here, derived in the design doc): FP64 operators agree to 1e-11 of the
+field scale (only summation order and FMA contraction differ); FP32 operators to 2e-6 of
+the scale; FP64 full solves to 1e-6 L and FP32 full solves to 2e-4 L."""
+import numpy as np
+import pytest
+
+from paper_2111_09859_gb300 import workloads as W
+from tests.helpers import base_params, gpu_params, oracle_grid, oracle_kw, to_np
+
+pytestmark = pytest.mark.gpu
+
+FP64_OP = 1e-11
+FP32_OP = 2e-6
+
+
+@pytest.fixture(scope="module")
+def wd():
+    import torch
+
+    assert torch.cuda.is_available()
+    from paper_2111_09859_gb300 import build, wd as _wd
+
+    build.build()
+    return _wd
+
+
+def exact_of(spec):
+    x = spec.xyz
+    if spec.name == "square":
+        return np.minimum.reduce([x[0], 1 - x[0], x[1], 1 - x[1]])
+    if spec.name in ("cylinder",):
+        return np.hypot(x[0], x[1]) - spec.meta.get("r_wall", 0.5)
+    if spec.name == "duct":
+        return np.minimum.reduce([x[1], 1 - x[1], x[2], 1 - x[2]])
+    if spec.name == "plate":
+        return x[1].copy()
+    if spec.name == "channel":
+        return np.minimum(x[1], 1 - x[1])
+    if spec.name == "ellipse":
+        return None
+    raise KeyError(spec.name)
+
+
+GRIDS = {
+    "square33": lambda: W.square(33),
+    "cyl33x64": lambda: W.cylinder(33, 64, 1.03 ** 8),
+    "duct12x8": lambda: W.duct(12, nx=8),
+    "plate": lambda: W.plate(16, 40, height=2.0, stretch=1.05),
+    "ellipse": lambda: W.ellipse(33, 64, 2.5),
+    "square71": lambda: W.square(71),
+}
+
+
+def scale(a):
+    return max(1.0, float(np.abs(a).max()))
+
+
+@pytest.mark.parametrize("gname", ["square33", "cyl33x64", "duct12x8", "plate", "ellipse"])
+@pytest.mark.parametrize("scheme", [1, 2, 4])
+def test_metrics(wd, oracle, gname, scheme):
+    spec = GRIDS[gname]()
+    og = oracle_grid(oracle, spec, scheme)
+    g = wd.Grid(spec, wd.FP64, scheme)
+    xi, J, dx = [to_np(t) for t in g.metrics()]
+    oxi, oJ, odx = og.metrics()
+    for l in range(spec.ndim):
+        for m in range(spec.ndim):
+            np.testing.assert_allclose(xi[l, m], oxi[l, m], atol=FP64_OP * scale(oxi[l, m]), rtol=0)
+        np.testing.assert_allclose(dx[l], odx[l], atol=FP64_OP * scale(odx[l]), rtol=0)
+    np.testing.assert_allclose(J, oJ, atol=FP64_OP * scale(oJ), rtol=0)
+
+
+@pytest.mark.parametrize("gname", ["square71", "cyl33x64", "duct12x8", "ellipse"])
+@pytest.mark.parametrize("scheme", [0, 1, 2, 3, 4])
+@pytest.mark.parametrize("prec", [0, 2])
+def test_derivative(wd, oracle, gname, scheme, prec):
+    spec = GRIDS[gname]()
+    og = oracle_grid(oracle, spec, scheme)
+    g = wd.Grid(spec, prec, scheme)
+    f = W.random_field(spec, 3) + 0.1 * W.random_field(spec, 4, smooth=False)
+    tol = FP64_OP if prec == 0 else FP32_OP
+    for d in range(spec.ndim):
+        ref = og.deriv(f, d, scheme)
+        out = to_np(g.derivative(g.as_field(f), d))
+        np.testing.assert_allclose(out, ref, atol=tol * scale(ref) * 10, rtol=0)
+
+
+@pytest.mark.parametrize("gname", ["square71", "cyl33x64", "duct12x8"])
+@pytest.mark.parametrize("alpha", [0.3, 0.49, 0.495])
+@pytest.mark.parametrize("prec", [0, 2])
+def test_filter(wd, oracle, gname, alpha, prec):
+    spec = GRIDS[gname]()
+    og = oracle_grid(oracle, spec, 1)
+    g = wd.Grid(spec, prec, 1)
+    f = W.random_field(spec, 5) + 0.3 * W.random_field(spec, 6, smooth=False)
+    tol = FP64_OP if prec == 0 else FP32_OP * 20    # alpha -> 1/2 amplifies float rounding
+    for d in range(spec.ndim):
+        ref = og.filter(f, d, alpha)
+        out = to_np(g.filter(g.as_field(f), d, alpha))
+        np.testing.assert_allclose(out, ref, atol=tol * scale(ref), rtol=0)
+
+
+RHS_CASES = [
+    ("square33", 1, dict(equation=0)),
+    ("square33", 1, dict(equation=1)),
+    ("square71", 2, dict(equation=1)),
+    ("cyl33x64", 4, dict(equation=1, curvature=1, alpha_f=0.495)),
+    ("cyl33x64", 4, dict(equation=0, curvature=1)),
+    ("duct12x8", 2, dict(equation=1)),
+    ("ellipse", 4, dict(equation=1)),
+    ("plate", 4, dict(equation=2)),
+]
+
+
+@pytest.mark.parametrize("case", range(len(RHS_CASES)))
+@pytest.mark.parametrize("prec", [0, 1, 2])
+@pytest.mark.parametrize("kind", [0, 1])
+def test_rhs(wd, oracle, case, prec, kind):
+    gname, scheme, kw = RHS_CASES[case]
+    spec = GRIDS[gname]()
+    prm = base_params(scheme, **kw)
+    og = oracle_grid(oracle, spec, scheme)
+    g = wd.Grid(spec, prec, scheme)
+    ex = exact_of(spec)
+    if ex is None:
+        ex = np.hypot(*spec.xyz) - 0.5
+    phi = og.apply_bc(ex + 0.02 * W.random_field(spec, 7))
+    okw = oracle_kw(scheme, prm)
+    if kind == 0:
+        R0, dt0 = og.rhs_hj(phi, **okw)
+    else:
+        R0, dt0 = og.rhs_poisson(phi, **okw)
+    R, dt = g.rhs(gpu_params(wd, scheme, prm), g.as_field(phi), kind)
+    tol = FP64_OP * 100 if prec == 0 else 1e-4
+    np.testing.assert_allclose(to_np(R), R0, atol=tol * scale(R0), rtol=0)
+    np.testing.assert_allclose(to_np(dt), dt0, atol=tol * scale(dt0), rtol=tol)
+
+
+@pytest.mark.parametrize("gname", ["square33", "cyl33x64", "duct12x8", "plate"])
+@pytest.mark.parametrize("prec", [0, 2])
+def test_spalding_and_bc(wd, oracle, gname, prec):
+    spec = GRIDS[gname]()
+    scheme = 4 if gname == "cyl33x64" else 1
+    og = oracle_grid(oracle, spec, scheme)
+    g = wd.Grid(spec, prec, scheme)
+    phip = 0.1 + 0.05 * W.random_field(spec, 8) ** 2
+    ref = og.spalding(phip, scheme=scheme)
+    out = to_np(g.spalding(g.as_field(phip)))
+    tol = FP64_OP if prec == 0 else FP32_OP
+    np.testing.assert_allclose(out, ref, atol=tol * scale(ref) * 10, rtol=0)
+    junk = W.random_field(spec, 9)
+    ref = og.apply_bc(junk)
+    out = to_np(g.apply_bc(g.as_field(junk)))
+    np.testing.assert_allclose(out, ref, atol=tol * scale(ref) * 10, rtol=0)
+
+
+STEP_CASES = [
+    ("square33", 1, dict(equation=0)),
+    ("square33", 1, dict(equation=1)),
+    ("cyl33x64", 4, dict(equation=1, curvature=1, alpha_f=0.495)),
+    ("duct12x8", 2, dict(equation=1)),
+    ("ellipse", 4, dict(equation=1)),
+    ("plate", 4, dict(equation=1)),
+]
+
+
+@pytest.mark.parametrize("case", range(len(STEP_CASES)))
+@pytest.mark.parametrize("prec", [0, 1])
+def test_pseudo_steps(wd, oracle, case, prec):
+    gname, scheme, kw = STEP_CASES[case]
+    spec = GRIDS[gname]()
+    prm = base_params(scheme, **kw)
+    og = oracle_grid(oracle, spec, scheme)
+    g = wd.Grid(spec, prec, scheme)
+    ex = exact_of(spec)
+    if ex is None:
+        ex = np.hypot(*spec.xyz) - 0.5
+    phi0 = og.apply_bc(ex + 0.02 * W.random_field(spec, 11))
+    ref, ost = og.hj_steps(phi0, 4, **oracle_kw(scheme, prm))
+    out, st = g.steps(gpu_params(wd, scheme, prm), g.as_field(phi0), 4, kind=0)
+    tol = 1e-10 if prec == 0 else 1e-5
+    np.testing.assert_allclose(to_np(out), ref, atol=tol * scale(ref), rtol=0)
+    assert abs(st["res_l2"] - ost["res_l2"]) <= (1e-8 if prec == 0 else 1e-2) * ost["res_l2"] + 1e-12
+    # Poisson pseudo steps from zero
+    refp, _ = og.poisson_steps(np.zeros(spec.N), 20, **oracle_kw(scheme, prm))
+    outp, _ = g.steps(gpu_params(wd, scheme, prm), g.as_field(np.zeros(spec.N)), 20, kind=1)
+    np.testing.assert_allclose(to_np(outp), refp, atol=tol * scale(refp), rtol=0)
+
+
+SOLVE_CASES = [
+    # name, spec, scheme, params, precision, tolerance (x L)
+    ("square65-E4-std-fp64", lambda: W.square(65), 1, dict(equation=0), 0, 1e-6),
+    ("square65-E4-lad-fp32", lambda: W.square(65), 1, dict(equation=1, tol_l2=1e-7), 2, 2e-4),
+    ("cyl-C6-lad-curv-fp64", lambda: W.cylinder(49, 96, 1.03 ** (256 / 48)), 4,
+     dict(equation=1, curvature=1, alpha_f=0.495), 0, 1e-6),
+    ("cyl-C6-lad-curv-fp32m64", lambda: W.cylinder(49, 96, 1.03 ** (256 / 48)), 4,
+     dict(equation=1, curvature=1, alpha_f=0.495, tol_l2=1e-7), 1, 2e-4),
+    ("duct-E6-lad-fp32", lambda: W.duct(24, nx=8), 2, dict(equation=1, tol_l2=1e-7), 2, 2e-4),
+    ("ellipse-C6-lad-fp32", lambda: W.ellipse(33, 64, 3.0), 4, dict(equation=1, tol_l2=1e-7), 2, 2e-4),
+]
+
+
+@pytest.mark.parametrize("case", range(len(SOLVE_CASES)), ids=[c[0] for c in SOLVE_CASES])
+def test_full_solve(wd, oracle, case):
+    name, mk, scheme, kw, prec, tol = SOLVE_CASES[case]
+    spec = mk()
+    prm = base_params(scheme, **kw)
+    og = oracle_grid(oracle, spec, scheme)
+    oprm = dict(prm, tol_l2=1e-12)
+    ref, ost = og.solve(**oracle_kw(scheme, oprm))
+    assert ost["converged"], ost
+    g = wd.Grid(spec, prec, scheme)
+    out, st = g.solve(gpu_params(wd, scheme, prm))
+    assert st["converged"], st
+    err = np.abs(to_np(out) - ref).max()
+    assert err <= tol * spec.L_ref, (name, err, st, ost)
