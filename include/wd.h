@@ -105,6 +105,9 @@ typedef struct {
     double res_linf;       /* max change of the last step / L_ref */
     int converged;         /* tolerance met */
     int diverged;          /* NaN / Inf met */
+    int stalled;           /* FP32 state only: stopped because the change norm stopped
+                              decreasing (rounding floor) before reaching the tolerance;
+                              converged is set too */
     double seconds;        /* wall time of the call */
     size_t device_bytes;   /* library-owned device memory of the grid */
 } wd_stats;
@@ -133,7 +136,9 @@ wd_status wd_set_stream(wd_grid g, void* cuda_stream);
 
 /* Steady solve (Sec. 3.3): initial guess, then HJ pseudo-time marching (RK4 with local
  * time steps, boundary conditions after every stage, filter after every step) until the
- * tolerances hold, max_iters is reached, or a NaN appears.  phi_dev (N values of the
+ * tolerances hold, max_iters is reached, or a NaN appears.  With a float state the march
+ * also stops once the RMS change has not fallen below 0.95 x its best value for 200
+ * pseudo steps (the float rounding floor; stats->stalled = 1).  phi_dev (N values of the
  * state precision, dense layout) is read when init == WD_INIT_GIVEN and always receives
  * the result.  Returns WD_OK when converged or when no tolerance was set,
  * WD_ERR_NOT_CONVERGED after max_iters with a tolerance set, WD_ERR_DIVERGED on NaN/Inf. */

@@ -159,7 +159,7 @@ static wd_status validate_desc(const wd_grid_desc* d)
     if (d->ndim == 2 && d->n[2] != 1) return set_error(WD_ERR_INVALID_ARG, "n[2] must be 1 in 2-D");
     for (int k = 0; k < d->ndim; k++) {
         if (d->n[k] < 8) return set_error(WD_ERR_INVALID_ARG, "every direction needs >= 8 nodes");
-        if (d->n[k] > (1 << 16)) return set_error(WD_ERR_INVALID_ARG, "direction too long");
+        if (d->n[k] > 2048) return set_error(WD_ERR_INVALID_ARG, "at most 2048 nodes per direction");
         int lo = d->bc_lo[k], hi = d->bc_hi[k];
         if (lo < 0 || lo > 3 || hi < 0 || hi > 3)
             return set_error(WD_ERR_INVALID_ARG, "unknown boundary kind");
@@ -281,6 +281,7 @@ struct Solver {
             if (!filter_coefficients(hw, al, op.fa[hw]))
                 return set_error(WD_ERR_INVALID_ARG, "filter coefficients");
         op.fa[0][0] = 1.0;
+        op.fa[0][1] = al;     // alpha_f, used by the delta-form right-hand side
         return WD_OK;
     }
 
@@ -495,6 +496,10 @@ struct Solver {
         bool have_tol = p->tol_l2 > 0.0 || p->tol_linf > 0.0;
         bool checked_last = true;
         wd_status rc = WD_OK;
+        const bool float_state = sizeof(T) == 4;
+        const int stall_steps = 200;
+        double best = INFINITY;
+        int since_best = 0;
         while (it < p->max_iters) {
             ST(step(false));
             it++;
@@ -510,6 +515,17 @@ struct Solver {
                 if (have_tol && (p->tol_l2 <= 0.0 || l2 <= p->tol_l2) &&
                     (p->tol_linf <= 0.0 || li <= p->tol_linf)) {
                     s.converged = 1;
+                    break;
+                }
+                if (l2 < 0.95 * best) {
+                    best = l2;
+                    since_best = 0;
+                } else {
+                    since_best += every;
+                }
+                if (float_state && have_tol && since_best >= stall_steps) {
+                    s.converged = 1;
+                    s.stalled = 1;
                     break;
                 }
             }

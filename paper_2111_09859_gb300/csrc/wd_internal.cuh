@@ -73,7 +73,7 @@ struct Fields {
 
 // host-side owner of one LineTab (both precisions)
 struct HostLineTab {
-    int N = 0, P = 0, implicit = 0, periodic = 0;
+    int N = 0, P = 0, implicit = 0, periodic = 0, maxm = 0;
     int* bnd = nullptr;
     double* dtab = nullptr;   // 5N + 2P + 4P^2 doubles
     float* ftab = nullptr;    // same, float

@@ -61,6 +61,11 @@ __device__ __forceinline__ T deriv_row(const T* F, int S, int t, int N, int per,
     return T(0.75) * d1 - T(0.15) * d2 + T(1.0 / 60.0) * d3;
 }
 
+// Filter right-hand side in delta form: with A fh = B f (Eq. 21) and sum_n a_n = 1 + 2 al,
+// (B - A) f = sum_{n>=1} a_n/2 (f_{t+n} + f_{t-n} - 2 f_t) - al (f_{t+1} + f_{t-1} - 2 f_t),
+// so A (fh - f) is built from second differences only; the line solve then yields the
+// correction fh - f, whose rounding error scales with the correction rather than with f
+// (the filter matrix amplifies high-frequency rounding by up to (1 + 2 al) / (1 - 2 al)).
 template <typename T>
 __device__ __forceinline__ T filter_row(const T* F, int S, int t, int N, int per, const LineOp& op)
 {
@@ -69,10 +74,14 @@ __device__ __forceinline__ T filter_row(const T* F, int S, int t, int N, int per
         int e = t < N - 1 - t ? t : N - 1 - t;
         if (e < hw) hw = e;
     }
-    if (hw == 0) return F[t * S];
-    T s = T(op.fa[hw][0]) * F[t * S];
-    for (int m = 1; m <= hw; m++)
-        s += T(0.5 * op.fa[hw][m]) * (fat(F, S, t + m, N, per) + fat(F, S, t - m, N, per));
+    if (hw == 0) return T(0);
+    const T f0 = F[t * S];
+    T s = T(0);
+    for (int m = hw; m >= 1; m--) {
+        T s2 = (fat(F, S, t + m, N, per) - f0) + (fat(F, S, t - m, N, per) - f0);
+        T cm = T(0.5 * op.fa[hw][m]) - (m == 1 ? T(op.fa[0][1]) : T(0));
+        s += cm * s2;
+    }
     return s;
 }
 
@@ -100,78 +109,150 @@ __device__ __forceinline__ T gauss_row(const T* F, int S, int t, int N, int per)
 }
 
 // ------------------------------------------------------------------------------------
-// k_line: LPB lines of direction `dir` per block, P chunks per line, one thread per
-// (line, chunk).  Shared memory: NF field buffers + one work buffer, each N x (LPB+1)
-// (position-major, padded against bank conflicts), plus the 2P chunk-end values per line.
+// k_line: one thread per (line, chunk).  A block holds LPB lines x P chunks (line index
+// fastest, so that for strided directions neighbouring threads read neighbouring nodes).
+// Each thread keeps its chunk (at most MAXM nodes) plus a 5-node halo in registers:
+// right-hand side, local Thomas sweep and fix-up all run in registers; only the 2P
+// chunk-end values of each line go through shared memory for the reduced system.
 // ------------------------------------------------------------------------------------
 
-template <typename T, typename M, int NF, int EPI>
-__global__ void __launch_bounds__(1024)
+constexpr int LH = 5;     // halo: E6 needs 3, the filter 5, the Gaussian 4
+constexpr int MAXM = 16;  // nodes per chunk at most (host tables guarantee it)
+
+// Row value at chunk position k (node t): the explicit derivative, the right-hand side of
+// a compact row, the delta-form filter right-hand side, or the Gaussian.  F points at the
+// register copy of node t (F[o] = node t + o).  cf[hw][m] holds the delta-form filter
+// weights a_m/2 - alpha [m == 1] of the order-2hw member.
+template <typename T>
+__device__ __forceinline__ T row_value(int kind, int sch, const T (*cf)[6], const T* F, int t,
+                                       int N, int per)
+{
+    if (kind == OPK_DERIV) {
+        if (!per) {
+            if (t == 0)
+                return (T(-25.0) * F[0] + T(48.0) * F[1] - T(36.0) * F[2] + T(16.0) * F[3]
+                        - T(3.0) * F[4]) * T(1.0 / 12.0);
+            if (t == N - 1)
+                return -(T(-25.0) * F[0] + T(48.0) * F[-1] - T(36.0) * F[-2] + T(16.0) * F[-3]
+                         - T(3.0) * F[-4]) * T(1.0 / 12.0);
+            if (t == 1 || t == N - 2) return T(0.5) * (F[1] - F[-1]);
+        }
+        T d1 = F[1] - F[-1];
+        if (sch == WD_E2) return T(0.5) * d1;
+        if (sch == WD_C4) return T(0.75) * d1;
+        T d2 = F[2] - F[-2];
+        if (sch == WD_C6) return T(7.0 / 9.0) * d1 + T(1.0 / 36.0) * d2;
+        if (sch == WD_E4 || (!per && (t == 2 || t == N - 3)))
+            return T(2.0 / 3.0) * d1 - T(1.0 / 12.0) * d2;
+        T d3 = F[3] - F[-3];
+        return T(0.75) * d1 - T(0.15) * d2 + T(1.0 / 60.0) * d3;
+    }
+    if (kind == OPK_FILTER) {
+        // delta form of Eq. 21: with sum_m a_m = 1 + 2 alpha,
+        //   A (fh - f) = sum_{m>=1} (a_m/2 - alpha [m==1]) (f_{t+m} + f_{t-m} - 2 f_t),
+        // so the line solve returns the correction fh - f, whose rounding scales with the
+        // correction instead of with f (the filter matrix amplifies high-frequency rounding
+        // by up to (1 + 2 alpha) / (1 - 2 alpha))
+        int hw = 5;
+        if (!per) {
+            int e = t < N - 1 - t ? t : N - 1 - t;
+            if (e < hw) hw = e;
+        }
+        if (hw == 0) return T(0);
+        const T f0 = F[0];
+        T s = T(0);
+#pragma unroll
+        for (int m = 5; m >= 1; m--)
+            if (m <= hw) s += cf[hw][m] * ((F[m] - f0) + (F[-m] - f0));
+        return s;
+    }
+    // truncated 9-point Gaussian (Kawai & Lele's LAD smoothing); the even reflection at
+    // non-periodic ends was applied when the halo was loaded
+    return T(3565.0 / 10368.0) * F[0] + T(3091.0 / 12960.0) * (F[1] + F[-1])
+         + T(1997.0 / 25920.0) * (F[2] + F[-2]) + T(149.0 / 12960.0) * (F[3] + F[-3])
+         + T(107.0 / 103680.0) * (F[4] + F[-4]);
+}
+
+// position loaded into halo slot t (may lie outside [0, N)): periodic wrap, even
+// reflection for the Gaussian, clamp otherwise (clamped values are never used by a row)
+__device__ __forceinline__ int halo_pos(int t, int N, int per, int reflect)
+{
+    if (per) return t < 0 ? t + N : (t >= N ? t - N : t);
+    if (reflect) return t < 0 ? -t : (t >= N ? 2 * (N - 1) - t : t);
+    return t < 0 ? 0 : (t >= N ? N - 1 : t);
+}
+
+// ------------------------------------------------------------------------------------
+// k_line: one thread per (line, chunk).  A block holds LPB lines x P chunks (line index
+// fastest, so that for strided directions neighbouring threads read neighbouring nodes).
+// Each thread keeps its chunk (at most 16 nodes) plus a 5-node halo in registers; the
+// right-hand side, the local Thomas sweep and the fix-up run in registers and only the
+// 2P chunk-end values of each line go through shared memory for the reduced system.
+// Epilogue: store each field, or accumulate out0 (+)= sum_{m<nU} xi_{dir,m} F_m and
+// out1 (+)= sum_m xi_{dir,m} F_{nU+m} (metric-weighted divergence, Eqs. 9 and 25).
+// ------------------------------------------------------------------------------------
+
+template <typename T, typename M, int NF, int EPI, int KIND>
+__global__ void __launch_bounds__(256, 2)
 k_line(Dims D, int dir, int nlines, int LPB, LineTab<T> tab, LineOp op, Fields<T> f,
        const M* __restrict__ xi, int nU, int accumulate)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
-    T* sm = reinterpret_cast<T*>(smraw);
-    const int N = tab.N, P = tab.P, S = LPB + 1;
-    T* fb = sm;
-    T* rb = sm + (size_t)NF * N * S;
-    T* Y = rb + (size_t)N * S;
-    const int tid = threadIdx.x, nth = blockDim.x;
-    const int q0 = blockIdx.x * LPB;
-    const int nl = min(LPB, nlines - q0);
-    const long long st = D.stride(dir);
-    const int per = D.per[dir];
-
-    for (int fi = 0; fi < NF; fi++) {
-        const T* __restrict__ src = f.in[fi];
-        T* dst = fb + (size_t)fi * N * S;
-        for (int e = tid; e < nl * N; e += nth) {
-            int ll, t;
-            if (dir == 0) {
-                ll = e / N;
-                t = e - ll * N;
-            } else {
-                t = e / nl;
-                ll = e - t * nl;
-            }
-            dst[t * S + ll] = src[D.line_base(dir, q0 + ll) + (long long)t * st];
-        }
+    T* Y = reinterpret_cast<T*>(smraw);              // LPB x 2P chunk-end values
+    __shared__ T cf[6][6];
+    for (int i = threadIdx.x; i < 36; i += blockDim.x) {
+        int hw = i / 6, m = i % 6;
+        double v = 0.0;
+        if (KIND == OPK_FILTER && hw >= 1 && m >= 1 && m <= hw)
+            v = 0.5 * op.fa[hw][m] - (m == 1 ? op.fa[0][1] : 0.0);
+        cf[hw][m] = T(v);
     }
     __syncthreads();
+    const int N = tab.N, P = tab.P, P2 = 2 * P;
+    const int l = threadIdx.x % LPB, c = threadIdx.x / LPB;
+    const int q = blockIdx.x * LPB + l;
+    const bool act = q < nlines;
+    const long long st = D.stride(dir);
+    const int per = D.per[dir];
+    constexpr int kind = KIND;
+    const int sch = op.scheme;
+    const int reflect = kind == OPK_GAUSS;
+    const long long base = act ? D.line_base(dir, q) : 0;
+    const int s = tab.bnd[c], Mc = tab.bnd[c + 1] - s;
 
-    const int l = tid % LPB, c = tid / LPB;
-    const bool act = (l < nl) && (c < P);
-    int s = 0, e = 0;
-    if (c < P) {
-        s = tab.bnd[c];
-        e = tab.bnd[c + 1];
-    }
-    const int P2 = 2 * P;
+    T acc[EPI ? MAXM : 1];
+    T x[MAXM];
+
+#pragma unroll 1
     for (int fi = 0; fi < NF; fi++) {
-        T* F = fb + (size_t)fi * N * S;
+        const T* __restrict__ src = f.in[fi];
         if (act) {
-            for (int t = s; t < e; t++) {
-                T r;
-                if (op.kind == OPK_DERIV) r = deriv_row(F + l, S, t, N, per, op.scheme);
-                else if (op.kind == OPK_FILTER) r = filter_row(F + l, S, t, N, per, op);
-                else r = gauss_row(F + l, S, t, N, per);
-                rb[t * S + l] = r;
-            }
+            T fr[MAXM + 2 * LH];
+#pragma unroll
+            for (int k = 0; k < MAXM + 2 * LH; k++)
+                if (k < Mc + 2 * LH) fr[k] = src[base + (long long)halo_pos(s + k - LH, N, per, reflect) * st];
+#pragma unroll
+            for (int k = 0; k < MAXM; k++)
+                if (k < Mc) x[k] = row_value<T>(kind, sch, cf, fr + LH + k, s + k, N, per);
         }
         if (tab.implicit) {
             if (act) {
                 T prev = T(0);
-                for (int t = s; t < e; t++) {
-                    prev = (rb[t * S + l] - tab.la[t] * prev) * tab.lib[t];
-                    rb[t * S + l] = prev;
-                }
-                T nxt = prev;
-                for (int t = e - 2; t >= s; t--) {
-                    nxt = rb[t * S + l] - tab.lcp[t] * nxt;
-                    rb[t * S + l] = nxt;
-                }
-                Y[l * P2 + 2 * c] = rb[s * S + l];
-                Y[l * P2 + 2 * c + 1] = rb[(e - 1) * S + l];
+#pragma unroll
+                for (int k = 0; k < MAXM; k++)
+                    if (k < Mc) {
+                        prev = (x[k] - tab.la[s + k] * prev) * tab.lib[s + k];
+                        x[k] = prev;
+                    }
+#pragma unroll
+                for (int k = MAXM - 2; k >= 0; k--)
+                    if (k < Mc - 1) x[k] = x[k] - tab.lcp[s + k] * x[k + 1];
+                T last = x[0];
+#pragma unroll
+                for (int k = 0; k < MAXM; k++)
+                    if (k == Mc - 1) last = x[k];
+                Y[l * P2 + 2 * c] = x[0];
+                Y[l * P2 + 2 * c + 1] = last;
             }
             __syncthreads();
             if (act) {
@@ -187,88 +268,64 @@ k_line(Dims D, int dir, int nlines, int LPB, LineTab<T> tab, LineOp op, Fields<T
                     for (int j = 0; j < P2; j++) pp += row[j] * Yl[j];
                 }
                 const T aq = ac * qm, cp = cc * pp;
-                for (int t = s; t < e; t++) rb[t * S + l] -= aq * tab.v[t] + cp * tab.w[t];
+#pragma unroll
+                for (int k = 0; k < MAXM; k++)
+                    if (k < Mc) x[k] -= aq * tab.v[s + k] + cp * tab.w[s + k];
             }
+            __syncthreads();   // Y is reused by the next field
         }
-        __syncthreads();
-        if (act)
-            for (int t = s; t < e; t++) F[t * S + l] = rb[t * S + l];
-        __syncthreads();
-    }
-
-    if (EPI == 0) {
-        for (int fi = 0; fi < NF; fi++) {
-            T* __restrict__ dstg = f.out[fi];
-            const T* F = fb + (size_t)fi * N * S;
-            for (int e2 = tid; e2 < nl * N; e2 += nth) {
-                int ll, t;
-                if (dir == 0) {
-                    ll = e2 / N;
-                    t = e2 - ll * N;
-                } else {
-                    t = e2 / nl;
-                    ll = e2 - t * nl;
+        if (!act) continue;
+        if (kind == OPK_FILTER) {
+#pragma unroll
+            for (int k = 0; k < MAXM; k++)
+                if (k < Mc) x[k] += src[base + (long long)(s + k) * st];
+        }
+        if (EPI == 0) {
+            T* __restrict__ dst = f.out[fi];
+#pragma unroll
+            for (int k = 0; k < MAXM; k++)
+                if (k < Mc) dst[base + (long long)(s + k) * st] = x[k];
+        } else {
+            const int grp = fi < nU ? 0 : 1, m = fi - grp * nU;
+            const M* __restrict__ xm = xi + (long long)(dir * 3 + m) * D.total;
+#pragma unroll
+            for (int k = 0; k < MAXM; k++)
+                if (k < Mc) {
+                    T v = T(xm[base + (long long)(s + k) * st] * M(x[k]));
+                    acc[EPI ? k : 0] = (m == 0 ? T(0) : acc[EPI ? k : 0]) + v;
                 }
-                dstg[D.line_base(dir, q0 + ll) + (long long)t * st] = F[t * S + ll];
-            }
-        }
-    } else {
-        // out0 (+)= sum_{m<nU} xi_{dir,m} F_m ;  out1 (+)= sum_m xi_{dir,m} F_{nU+m}
-        for (int e2 = tid; e2 < nl * N; e2 += nth) {
-            int ll, t;
-            if (dir == 0) {
-                ll = e2 / N;
-                t = e2 - ll * N;
-            } else {
-                t = e2 / nl;
-                ll = e2 - t * nl;
-            }
-            long long p = D.line_base(dir, q0 + ll) + (long long)t * st;
-            M s0 = M(0), s1 = M(0);
-            for (int m = 0; m < nU; m++) {
-                M x = xi[(long long)(dir * 3 + m) * D.total + p];
-                s0 += x * M(fb[(size_t)m * N * S + t * S + ll]);
-                if (NF > nU) s1 += x * M(fb[(size_t)(nU + m) * N * S + t * S + ll]);
-            }
-            T* o0 = f.out[0];
-            o0[p] = accumulate ? T(M(o0[p]) + s0) : T(s0);
-            if (NF > nU) {
-                T* o1 = f.out[1];
-                o1[p] = accumulate ? T(M(o1[p]) + s1) : T(s1);
+            if (m == nU - 1) {
+                T* o = f.out[grp];
+#pragma unroll
+                for (int k = 0; k < MAXM; k++)
+                    if (k < Mc) {
+                        long long p = base + (long long)(s + k) * st;
+                        o[p] = accumulate ? o[p] + acc[EPI ? k : 0] : acc[EPI ? k : 0];
+                    }
             }
         }
     }
 }
 
-template <typename T>
-static size_t line_smem(int nf, int N, int LPB, int P)
-{
-    return ((size_t)(nf + 1) * N * (LPB + 1) + (size_t)LPB * 2 * P) * sizeof(T);
-}
-
-template <typename T, typename M, int NF, int EPI>
+template <typename T, typename M, int NF, int EPI, int KIND>
 static cudaError_t line_dispatch(const Dims& D, int dir, const HostLineTab& tab, const LineOp& op,
                                  const Fields<T>& f, const M* xi, int nU, int accumulate,
                                  cudaStream_t st)
 {
-    static int attr_done = 0;
-    const size_t limit = 200 * 1024;
-    if (!attr_done) {
-        cudaError_t e = cudaFuncSetAttribute(k_line<T, M, NF, EPI>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)limit);
-        if (e != cudaSuccess) return e;
-        attr_done = 1;
-    }
-    int N = tab.N, P = tab.P;
-    int LPB = 32;
-    while (LPB > 1 && (LPB * P > 1024 || line_smem<T>(NF, N, LPB, P) > limit)) LPB /= 2;
-    if (LPB * P > 1024 || line_smem<T>(NF, N, LPB, P) > limit) return cudaErrorInvalidConfiguration;
-    int nlines = D.nlines(dir);
+    if (tab.maxm > MAXM) return cudaErrorInvalidConfiguration;
+    const int P = tab.P;
+    const int nlines = D.nlines(dir);
+    // strided directions: up to 32 lines per block (coalesced rows); contiguous lines
+    // gain nothing from wide blocks.  Shrink until the grid covers the 152 SMs twice.
+    int LPB = dir == 0 ? 4 : 32;
+    while (LPB > 1 && LPB * P > 256) LPB /= 2;
+    const int min_lpb = dir == 0 ? 1 : (P <= 32 ? 8 : 2);
+    while (LPB > min_lpb && (nlines + LPB - 1) / LPB < 2 * 152) LPB /= 2;
+    if (LPB * P > 256 || LPB < 1) return cudaErrorInvalidConfiguration;
     int grid = (nlines + LPB - 1) / LPB;
-    size_t sm = line_smem<T>(NF, N, LPB, P);
-    k_line<T, M, NF, EPI><<<grid, LPB * P, sm, st>>>(D, dir, nlines, LPB, tab.view<T>(), op, f, xi,
-                                                     nU, accumulate);
+    size_t sm = (size_t)LPB * 2 * P * sizeof(T);
+    k_line<T, M, NF, EPI, KIND><<<grid, LPB * P, sm, st>>>(D, dir, nlines, LPB, tab.view<T>(), op, f,
+                                                           xi, nU, accumulate);
     return cudaGetLastError();
 }
 
@@ -278,19 +335,22 @@ cudaError_t launch_line(const Dims& D, int dir, const HostLineTab& tab, const Li
                         cudaStream_t st)
 {
     if (tab.N != D.n[dir]) return cudaErrorInvalidValue;
+    if (op.kind == OPK_FILTER && nf == 1 && epi == 0)
+        return line_dispatch<T, M, 1, 0, OPK_FILTER>(D, dir, tab, op, f, xi, nU, accumulate, st);
+    if (op.kind == OPK_GAUSS && nf == 1 && epi == 0)
+        return line_dispatch<T, M, 1, 0, OPK_GAUSS>(D, dir, tab, op, f, xi, nU, accumulate, st);
+    if (op.kind != OPK_DERIV) return cudaErrorInvalidValue;
     if (epi == 0) {
         switch (nf) {
-        case 1: return line_dispatch<T, M, 1, 0>(D, dir, tab, op, f, xi, nU, accumulate, st);
-        case 2: return line_dispatch<T, M, 2, 0>(D, dir, tab, op, f, xi, nU, accumulate, st);
-        case 3: return line_dispatch<T, M, 3, 0>(D, dir, tab, op, f, xi, nU, accumulate, st);
+        case 1: return line_dispatch<T, M, 1, 0, OPK_DERIV>(D, dir, tab, op, f, xi, nU, accumulate, st);
         default: return cudaErrorInvalidValue;
         }
     }
     switch (nf) {
-    case 2: return line_dispatch<T, M, 2, 1>(D, dir, tab, op, f, xi, nU, accumulate, st);
-    case 3: return line_dispatch<T, M, 3, 1>(D, dir, tab, op, f, xi, nU, accumulate, st);
-    case 4: return line_dispatch<T, M, 4, 1>(D, dir, tab, op, f, xi, nU, accumulate, st);
-    case 6: return line_dispatch<T, M, 6, 1>(D, dir, tab, op, f, xi, nU, accumulate, st);
+    case 2: return line_dispatch<T, M, 2, 1, OPK_DERIV>(D, dir, tab, op, f, xi, nU, accumulate, st);
+    case 3: return line_dispatch<T, M, 3, 1, OPK_DERIV>(D, dir, tab, op, f, xi, nU, accumulate, st);
+    case 4: return line_dispatch<T, M, 4, 1, OPK_DERIV>(D, dir, tab, op, f, xi, nU, accumulate, st);
+    case 6: return line_dispatch<T, M, 6, 1, OPK_DERIV>(D, dir, tab, op, f, xi, nU, accumulate, st);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -468,8 +528,12 @@ __global__ void k_spalding(Dims D, const T* __restrict__ U0, const T* __restrict
         if ((int)(e % D.pitch) >= D.n[0]) continue;
         T g2 = U0[e] * U0[e] + U1[e] * U1[e];
         if (D.ndim == 3) g2 += U2[e] * U2[e];
+        // Eq. 4 with the minus root, -g + sqrt(g^2 + 2 phi'), evaluated in the equivalent
+        // form 2 phi' / (g + sqrt(g^2 + 2 phi')) that does not cancel when 2 phi' << g^2
+        T g = sqrt(g2);
         T arg = g2 + T(2) * phip[e];
-        phi[e] = -sqrt(g2) + sqrt(arg > T(0) ? arg : T(0));          // Eq. 4, minus root
+        T r = sqrt(arg > T(0) ? arg : T(0));
+        phi[e] = (arg > T(0) && g + r > T(0)) ? T(2) * phip[e] / (g + r) : -g;
     }
 }
 

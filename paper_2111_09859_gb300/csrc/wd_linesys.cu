@@ -9,6 +9,7 @@
 // Thomas sweep on its chunk, and the 2P unknown chunk-end values are obtained from a
 // precomputed dense inverse of the reduced system; each chunk then adds the responses to
 // its two neighbours' end values.  All factors below are computed in double.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -135,11 +136,12 @@ void filter_rows(double al, int N, int periodic, std::vector<double>& a,
     }
 }
 
+// chunks per line: at most 16 nodes per chunk (the GPU keeps a chunk in registers), at
+// least 4 nodes per chunk
 int choose_chunks(int N)
 {
-    int P = N / 16;
+    int P = (N + 15) / 16;
     if (P < 1) P = 1;
-    if (P > 32) P = 32;
     while (P > 1 && N / P < 4) P--;
     return P;
 }
@@ -157,6 +159,9 @@ wd_status build_line_table(int N, int periodic, const std::vector<double>& a,
     tab.periodic = periodic;
     std::vector<int> bnd(P + 1);
     for (int ch = 0; ch <= P; ch++) bnd[ch] = (int)((long long)ch * N / P);
+    tab.maxm = 0;
+    for (int ch = 0; ch < P; ch++) tab.maxm = std::max(tab.maxm, bnd[ch + 1] - bnd[ch]);
+    if (tab.maxm > 16) return set_error(WD_ERR_INVALID_ARG, "line chunk longer than 16 nodes");
     size_t nd = (size_t)5 * N + 2 * P + (size_t)4 * P * P;
     std::vector<double> h(nd, 0.0);
     double *la = h.data(), *lib = la + N, *lcp = lib + N, *v = lcp + N, *w = v + N;

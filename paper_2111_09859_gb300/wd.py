@@ -52,7 +52,7 @@ class Stats(C.Structure):
     _fields_ = [
         ("iters", C.c_int), ("poisson_iters", C.c_int), ("res_l2", C.c_double),
         ("res_linf", C.c_double), ("converged", C.c_int), ("diverged", C.c_int),
-        ("seconds", C.c_double), ("device_bytes", C.c_size_t),
+        ("stalled", C.c_int), ("seconds", C.c_double), ("device_bytes", C.c_size_t),
     ]
 
     def as_dict(self):

@@ -150,8 +150,11 @@ def test_spalding_and_bc(wd, oracle, gname, prec):
     phip = 0.1 + 0.05 * W.random_field(spec, 8) ** 2
     ref = og.spalding(phip, scheme=scheme)
     out = to_np(g.spalding(g.as_field(phip)))
-    tol = FP64_OP if prec == 0 else FP32_OP
-    np.testing.assert_allclose(out, ref, atol=tol * scale(ref) * 10, rtol=0)
+    # float: the one-sided wall derivative of phi' (weights summing to 128/12 in absolute
+    # value) times |grad eta| ~ 1/dr0 turns the float rounding of phi' ~ 0.1 into ~5e-5 of
+    # |grad phi'| on the stretched O-grid's wall row; Eq. 4 passes it on at the same size
+    tol = FP64_OP * 10 if prec == 0 else 2e-4
+    np.testing.assert_allclose(out, ref, atol=tol * scale(ref), rtol=0)
     junk = W.random_field(spec, 9)
     ref = og.apply_bc(junk)
     out = to_np(g.apply_bc(g.as_field(junk)))
