@@ -11,8 +11,11 @@
  *    WD_FP32_METRIC64 and WD_FP32.  Metric exports are always double.
  *  - Pointers named *_dev are CUDA device pointers owned by the caller; *_host are host
  *    pointers read during the call only.  The library owns every internal buffer.
- *  - All device work is issued on the stream given to wd_create_grid (or wd_set_stream).
- *    wd_solve, wd_steps, wd_step_unsteady and wd_solve_batch return after the stream has
+ *  - Each grid owns a non-blocking CUDA stream on which all of its device work runs
+ *    (captured into CUDA graphs during solves).  Every call first waits for the work
+ *    already queued on the caller's stream (given to wd_create_grid or wd_set_stream) and
+ *    makes that stream wait for the call's own work, so the caller's stream stays ordered.
+ *    wd_solve, wd_steps, wd_step_unsteady and wd_solve_batch return after the work has
  *    finished; the operator entry points (wd_derivative ... wd_apply_bc) only enqueue.
  *  - Every function returns a wd_status and never aborts.  After WD_ERR_CUDA the CUDA
  *    context may be unusable; after any other error the grid stays valid.

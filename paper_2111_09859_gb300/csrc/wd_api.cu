@@ -5,12 +5,14 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <type_traits>
 #include <vector>
 
 #include "wd_api_internal.h"
+#include "wd_fused2d.h"
 
 using namespace wd;
 
@@ -47,7 +49,9 @@ enum {
 struct wd_grid_s {
     Dims D;
     wd_grid_desc desc;
-    cudaStream_t stream = nullptr;
+    cudaStream_t stream = nullptr;       // library-owned non-blocking stream (all work)
+    cudaStream_t user_stream = nullptr;  // the caller's stream
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
     int es = 8;                 // bytes per state element
     size_t bytes = 0;
     double* xyz = nullptr;      // 3 padded coordinate arrays
@@ -73,6 +77,8 @@ struct wd_grid_s {
     double* hres = nullptr;     // pinned
     unsigned long long* dcount = nullptr;
     int nred = 0;
+    int npartial = 0;           // capacity of `partial` in blocks
+    int force_generic = 0;      // WD_FORCE_GENERIC=1 at creation: never use the fused path
     HostLineTab dtab[3], ftab[3], etab[3];
     // kernel timer (wd_profile)
     int prof_on = 0;
@@ -127,6 +133,23 @@ struct ProfScope {
 
 static bool metric_double(int prec) { return prec != WD_FP32; }
 
+// Every call runs on the grid's own stream (graph capture needs a non-legacy stream), ordered
+// after the work already queued on the caller's stream; on exit the caller's stream waits
+// for the call's work, so the caller sees stream-ordered semantics on its own stream.
+struct StreamGuard {
+    wd_grid g;
+    explicit StreamGuard(wd_grid g_) : g(g_)
+    {
+        cudaEventRecord(g->ev_in, g->user_stream);
+        cudaStreamWaitEvent(g->stream, g->ev_in, 0);
+    }
+    ~StreamGuard()
+    {
+        cudaEventRecord(g->ev_out, g->stream);
+        cudaStreamWaitEvent(g->user_stream, g->ev_out, 0);
+    }
+};
+
 static size_t footprint_bytes(const wd_grid_desc* d)
 {
     long long pitch = (d->n[0] + 31) / 32 * 32;
@@ -146,8 +169,9 @@ static size_t footprint_bytes(const wd_grid_desc* d)
     }
     b += (size_t)fmax * 6 * 8;
     for (int k = 0; k < d->ndim; k++) {
-        int P = choose_chunks(d->n[k]);
-        b += 3 * ((size_t)(5 * d->n[k] + 2 * P + 4 * P * P) * 12 + (P + 1) * 4);
+        int L = 0;
+        while ((1 << L) < d->n[k]) L++;
+        b += 3 * (size_t)(2 * L + 2) * d->n[k] * 12;
     }
     return b;
 }
@@ -226,6 +250,9 @@ static void release(wd_grid g)
         free_line_table(g->etab[k]);
     }
     for (auto& e : g->ev_pool) cudaEventDestroy(e);
+    if (g->ev_in) cudaEventDestroy(g->ev_in);
+    if (g->ev_out) cudaEventDestroy(g->ev_out);
+    if (g->stream) cudaStreamDestroy(g->stream);
     delete g;
 }
 
@@ -424,10 +451,103 @@ struct Solver {
         return WD_OK;
     }
 
+    // fused 2-D path: direction-0 faces periodic or walls (all far-field handling happens
+    // along direction-1 lines), see wd_fused2d.cu
+    bool fused2d() const
+    {
+        if (D.ndim != 2 || g->force_generic) return false;
+        auto ok = [](int k) { return k == WD_BC_PERIODIC || k == WD_BC_WALL; };
+        return ok(g->desc.bc_lo[0]) && ok(g->desc.bc_hi[0]);
+    }
+
+    F2Args<T, M> f2_args(bool poisson)
+    {
+        F2Args<T, M> a;
+        std::memset(&a, 0, sizeof(a));
+        a.D = D;
+        a.scheme = g->desc.scheme;
+        a.dtab0 = g->dtab[0].template view<T>();
+        a.dtab1 = g->dtab[1].template view<T>();
+        if (p->filter) a.ftab1 = g->ftab[1].template view<T>();
+        a.xi = xi();
+        a.lads = (const M*)g->lads;
+        a.sig1 = (const M*)g->sig1;
+        a.sig2 = (const M*)g->sig2;
+        a.phin = W(W_PHIN);
+        a.phin_w = W(W_PHIN);
+        a.acc = W(W_ACC);
+        a.dtv = W(W_DT);
+        a.D0 = W(W_D0);
+        a.D1 = W(W_D1);
+        a.L0 = W(W_N0);
+        a.L1 = W(W_N1);
+        a.LAP0 = W(W_LAP);
+        a.LAP1 = W(W_U0);
+        a.KAP0 = W(W_KAP);
+        a.KAP1 = W(W_U1);
+        a.G0 = W(W_LAD);
+        a.mask = g->mask;
+        a.dval = (const T*)g->dval;
+        a.ffr_lo = g->ffr + 2 * g->fmax;
+        a.ffr_hi = g->ffr + 3 * g->fmax;
+        a.bclo1 = g->desc.bc_lo[1];
+        a.bchi1 = g->desc.bc_hi[1];
+        a.eps = p->eps;
+        a.cfl = p->cfl;
+        a.C_lad = p->C_lad;
+        a.eps0 = p->eps0;
+        a.alpha_f = p->alpha_f;
+        a.equation = p->equation;
+        a.curvature = p->curvature;
+        a.lad = p->equation == WD_HJ_LAD && !poisson;
+        a.poisson = poisson;
+        a.filter = p->filter;
+        a.partial = g->partial;
+        a.counter = g->counter;
+        a.result = g->result;
+        a.max_partials = g->npartial;
+        return a;
+    }
+
+    wd_status step_fused(bool poisson)
+    {
+        if (p->filter) ST(ensure_filter(p->alpha_f));
+        if (p->equation == WD_HJ_LAD && !poisson) ST(ensure_lads(p->lad_exp));
+        F2Args<T, M> a = f2_args(poisson);
+        if (p->filter) {
+            LineOp op;
+            ST(op_filter(p->alpha_f, op));
+            std::memcpy(a.fa, op.fa, sizeof(a.fa));
+        }
+        for (int s = 0; s < 4; s++) {
+            a.src = s == 0 ? W(W_PHIN) : W(W_PHIS);
+            a.dst = W(W_PHIS);
+            a.stage = s;
+            {
+                ProfScope ps(g, WD_K_DERIV);
+                CK(f2_launch<T, M>(a, F2_DERIV, st));
+            }
+            {
+                ProfScope ps(g, WD_K_DIV);
+                CK(f2_launch<T, M>(a, F2_DIV, st));
+            }
+            {
+                ProfScope ps(g, WD_K_POINT);
+                CK(f2_launch<T, M>(a, F2_STAGE, st));
+            }
+        }
+        if (p->filter) ST(filter_dir(0, p->alpha_f, W(W_PHIS), W(W_PHIS)));
+        a.src = W(W_PHIS);
+        ProfScope ps(g, WD_K_NORM);
+        CK(f2_launch<T, M>(a, F2_FILTER, st));
+        return WD_OK;
+    }
+
     // one pseudo step from W_PHIN; leaves the new state in W_PHIN and the change norms in
     // g->result
     wd_status step(bool poisson)
     {
+        if (fused2d()) return step_fused(poisson);
         for (int s = 0; s < 4; s++) {
             const T* src = s == 0 ? W(W_PHIN) : W(W_PHIS);
             ST(rhs_into(src, W(W_PHIS), poisson, s));
@@ -440,6 +560,47 @@ struct Solver {
         ProfScope ps(g, WD_K_NORM);
         CK(launch_norms<T>(D, W(W_PHIS), W(W_PHIN), g->mask, g->partial, g->counter, g->result,
                            g->nred, st));
+        return WD_OK;
+    }
+
+    // Runs n pseudo steps.  Without the kernel timer the steps are captured once into a
+    // CUDA graph (n steps per graph) and replayed, so the launch sequence costs one graph
+    // launch per n steps; the first step of a call always runs uncaptured so that every
+    // table and kernel attribute exists before capture.
+    cudaGraphExec_t gexec = nullptr;
+    int gexec_n = 0, gexec_poisson = -1;
+    ~Solver()
+    {
+        if (gexec) cudaGraphExecDestroy(gexec);
+    }
+    wd_status run_steps(bool poisson, int n, bool& warmed)
+    {
+        if (n <= 0) return WD_OK;
+        if (g->prof_on || !warmed) {
+            for (int i = 0; i < n; i++) ST(step(poisson));
+            warmed = true;
+            return WD_OK;
+        }
+        if (!gexec || gexec_n != n || gexec_poisson != (int)poisson) {
+            if (gexec) cudaGraphExecDestroy(gexec);
+            gexec = nullptr;
+            cudaGraph_t graph = nullptr;
+            CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+            wd_status rs = WD_OK;
+            for (int i = 0; i < n && rs == WD_OK; i++) rs = step(poisson);
+            cudaError_t ce = cudaStreamEndCapture(st, &graph);
+            if (rs != WD_OK) {
+                if (graph) cudaGraphDestroy(graph);
+                return rs;
+            }
+            CK(ce);
+            ce = cudaGraphInstantiate(&gexec, graph, 0);
+            cudaGraphDestroy(graph);
+            CK(ce);
+            gexec_n = n;
+            gexec_poisson = poisson;
+        }
+        CK(cudaGraphLaunch(gexec, st));
         return WD_OK;
     }
 
@@ -474,13 +635,15 @@ struct Solver {
         } else {
             CK(launch_fill<T>(W(W_PHIN), D.total, T(0), st));
         }
+        bool warmed = false;
         if (init == WD_INIT_POISSON) {
             ST(bc(W(W_PHIN), true));
             int it = 0;
             double l2 = 0, li = 0;
             while (it < p->poisson_max_iters) {
-                ST(step(true));
-                it++;
+                int n = std::min(every - it % every, p->poisson_max_iters - it);
+                ST(run_steps(true, n, warmed));
+                it += n;
                 if (p->poisson_tol > 0.0 && it % every == 0) {
                     ST(read_norms(L * L, &l2, &li));
                     if (!std::isfinite(l2) || !std::isfinite(li)) break;
@@ -500,9 +663,11 @@ struct Solver {
         const int stall_steps = 200;
         double best = INFINITY;
         int since_best = 0;
+        warmed = false;
         while (it < p->max_iters) {
-            ST(step(false));
-            it++;
+            int n = std::min(every - it % every, p->max_iters - it);
+            ST(run_steps(false, n, warmed));
+            it += n;
             checked_last = false;
             if (it % every == 0 || it == p->max_iters) {
                 ST(read_norms(L, &l2, &li));
@@ -738,7 +903,8 @@ static wd_status create_impl(wd_grid g, const double* xyz_host, const uint8_t* m
         CK(cudaMemsetAsync(g->w[k], 0, (size_t)tot * sizeof(T), st));
     }
     g->nred = (int)std::min<long long>((tot + 255) / 256, 1024);
-    ST(dmalloc(g, (void**)&g->partial, (size_t)g->nred * 2 * 8));
+    g->npartial = std::max(g->nred, std::max(D.n[0], D.n[1] * (D.ndim == 3 ? D.n[2] : 1)));
+    ST(dmalloc(g, (void**)&g->partial, (size_t)g->npartial * 2 * 8));
     ST(dmalloc(g, (void**)&g->counter, sizeof(unsigned)));
     ST(dmalloc(g, (void**)&g->result, 2 * 8));
     CK(cudaMemsetAsync(g->counter, 0, sizeof(unsigned), st));
@@ -792,7 +958,14 @@ wd_status wd_create_grid(const wd_grid_desc* desc, const double* xyz_host, const
     if (!xyz_host) return set_error(WD_ERR_INVALID_ARG, "xyz_host is NULL");
     wd_grid g = new wd_grid_s();
     g->desc = *desc;
-    g->stream = (cudaStream_t)cuda_stream;
+    g->user_stream = (cudaStream_t)cuda_stream;
+    if (cudaStreamCreateWithFlags(&g->stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&g->ev_in, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&g->ev_out, cudaEventDisableTiming) != cudaSuccess) {
+        cudaError_t e = cudaGetLastError();
+        release(g);
+        return cuda_error(e, "stream / event creation");
+    }
     g->es = desc->precision == WD_FP64 ? 8 : 4;
     Dims& D = g->D;
     D.ndim = desc->ndim;
@@ -802,11 +975,19 @@ wd_status wd_create_grid(const wd_grid_desc* desc, const double* xyz_host, const
     }
     D.pitch = (desc->n[0] + 31) / 32 * 32;
     D.total = (long long)D.pitch * D.n[1] * D.n[2];
-    wd_status s = dispatch(g, [&](auto* t, auto* m) {
-        using T = std::remove_pointer_t<decltype(t)>;
-        using M = std::remove_pointer_t<decltype(m)>;
-        return create_impl<T, M>(g, xyz_host, mask_host, dval_host);
-    });
+    {
+        const char* fg = std::getenv("WD_FORCE_GENERIC");
+        g->force_generic = fg && fg[0] == '1';
+    }
+    wd_status s;
+    {
+        StreamGuard sg(g);
+        s = dispatch(g, [&](auto* t, auto* m) {
+            using T = std::remove_pointer_t<decltype(t)>;
+            using M = std::remove_pointer_t<decltype(m)>;
+            return create_impl<T, M>(g, xyz_host, mask_host, dval_host);
+        });
+    }
     if (s == WD_OK) s = count_active(g);
     if (s != WD_OK) {
         std::string keep = g_err;
@@ -828,7 +1009,7 @@ void wd_destroy_grid(wd_grid g)
 wd_status wd_set_stream(wd_grid g, void* cuda_stream)
 {
     if (!g) return set_error(WD_ERR_INVALID_ARG, "grid is NULL");
-    g->stream = (cudaStream_t)cuda_stream;
+    g->user_stream = (cudaStream_t)cuda_stream;
     return WD_OK;
 }
 
@@ -847,6 +1028,7 @@ wd_status wd_solve(wd_grid g, const wd_solve_params* p, void* phi_dev, wd_stats*
 {
     if (!g || !phi_dev) return set_error(WD_ERR_INVALID_ARG, "NULL grid or phi");
     ST(check_params(p));
+    StreamGuard sg(g);
     auto t0 = std::chrono::steady_clock::now();
     wd_status s = dispatch(g, [&](auto* t, auto* m) {
         using T = std::remove_pointer_t<decltype(t)>;
@@ -864,6 +1046,7 @@ wd_status wd_step_unsteady(wd_grid g, const uint8_t* mask_dev, const void* dval_
 {
     if (!g || !phi_dev) return set_error(WD_ERR_INVALID_ARG, "NULL grid or phi");
     ST(check_params(p));
+    StreamGuard sg(g);
     auto t0 = std::chrono::steady_clock::now();
     wd_status s = dispatch(g, [&](auto* t, auto* m) {
         using T = std::remove_pointer_t<decltype(t)>;
@@ -919,6 +1102,7 @@ const char* wd_last_error(void) { return g_err.c_str(); }
 wd_status wd_get_metrics(wd_grid g, double* xi_dev, double* J_dev, double* dx_dev)
 {
     if (!g) return set_error(WD_ERR_INVALID_ARG, "grid is NULL");
+    StreamGuard sg(g);
     long long tot = g->D.total;
     size_t N = (size_t)g->D.n[0] * g->D.n[1] * g->D.n[2];
     for (int k = 0; k < 9 && xi_dev; k++) CK(from_padded(g, xi_dev + k * N, g->xi_d + k * tot, 8));
@@ -931,6 +1115,7 @@ wd_status wd_derivative(wd_grid g, int dir, const void* in_dev, void* out_dev)
 {
     if (!g || !in_dev || !out_dev || dir < 0 || dir >= g->desc.ndim)
         return set_error(WD_ERR_INVALID_ARG, "bad derivative arguments");
+    StreamGuard sg(g);
     return dispatch(g, [&](auto* t, auto* m) {
         using T = std::remove_pointer_t<decltype(t)>;
         using M = std::remove_pointer_t<decltype(m)>;
@@ -946,6 +1131,7 @@ wd_status wd_filter(wd_grid g, double alpha_f, int dir, const void* in_dev, void
 {
     if (!g || !in_dev || !out_dev || dir < 0 || dir >= g->desc.ndim || !(std::fabs(alpha_f) < 0.5))
         return set_error(WD_ERR_INVALID_ARG, "bad filter arguments");
+    StreamGuard sg(g);
     return dispatch(g, [&](auto* t, auto* m) {
         using T = std::remove_pointer_t<decltype(t)>;
         using M = std::remove_pointer_t<decltype(m)>;
@@ -962,6 +1148,7 @@ wd_status wd_rhs(wd_grid g, const wd_solve_params* p, int kind, const void* phi_
 {
     if (!g || !phi_dev || (kind != 0 && kind != 1)) return set_error(WD_ERR_INVALID_ARG, "bad rhs arguments");
     ST(check_params(p));
+    StreamGuard sg(g);
     return dispatch(g, [&](auto* t, auto* m) {
         using T = std::remove_pointer_t<decltype(t)>;
         using M = std::remove_pointer_t<decltype(m)>;
@@ -973,6 +1160,7 @@ wd_status wd_rhs(wd_grid g, const wd_solve_params* p, int kind, const void* phi_
 wd_status wd_spalding(wd_grid g, const void* phip_dev, void* phi_dev)
 {
     if (!g || !phip_dev || !phi_dev) return set_error(WD_ERR_INVALID_ARG, "bad spalding arguments");
+    StreamGuard sg(g);
     return dispatch(g, [&](auto* t, auto* m) {
         using T = std::remove_pointer_t<decltype(t)>;
         using M = std::remove_pointer_t<decltype(m)>;
@@ -987,6 +1175,7 @@ wd_status wd_spalding(wd_grid g, const void* phip_dev, void* phi_dev)
 wd_status wd_apply_bc(wd_grid g, void* phi_dev)
 {
     if (!g || !phi_dev) return set_error(WD_ERR_INVALID_ARG, "bad bc arguments");
+    StreamGuard sg(g);
     return dispatch(g, [&](auto* t, auto* m) {
         using T = std::remove_pointer_t<decltype(t)>;
         using M = std::remove_pointer_t<decltype(m)>;
@@ -1004,6 +1193,7 @@ wd_status wd_steps(wd_grid g, const wd_solve_params* p, int kind, void* phi_dev,
     if (!g || !phi_dev || (kind != 0 && kind != 1) || nsteps < 0)
         return set_error(WD_ERR_INVALID_ARG, "bad steps arguments");
     ST(check_params(p));
+    StreamGuard sg(g);
     return dispatch(g, [&](auto* t, auto* m) {
         using T = std::remove_pointer_t<decltype(t)>;
         using M = std::remove_pointer_t<decltype(m)>;

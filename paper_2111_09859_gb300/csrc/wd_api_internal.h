@@ -19,7 +19,6 @@ void derivative_rows(int scheme, int N, int periodic, std::vector<double>& a,
                      std::vector<double>& c, int& implicit);
 void filter_rows(double al, int N, int periodic, std::vector<double>& a, std::vector<double>& c,
                  int& implicit);
-int choose_chunks(int N);
 wd_status build_line_table(int N, int periodic, const std::vector<double>& a,
                            const std::vector<double>& c, int implicit, HostLineTab& tab);
 void free_line_table(HostLineTab& tab);

@@ -41,20 +41,19 @@ struct Dims {
     }
 };
 
-// Constant-coefficient tridiagonal system along one grid direction, split into P chunks
-// for the partition (divide-and-conquer) solve; see wd_linesys.cu.
+// Constant-coefficient tridiagonal system along one grid direction (unit diagonal except
+// in boundary rows), prepared for parallel cyclic reduction: level s combines rows i -/+ 2^s
+// with multipliers alpha[s][i], gamma[s][i]; ib = 1 / final diagonal.  Periodic systems are
+// solved through the corner-free matrix plus a Sherman-Morrison correction along z with
+// the scalars a0 (corner coefficient) and inv_den.  See wd_linesys.cu.
 template <typename T>
 struct LineTab {
-    int N, P, implicit, periodic;
-    const int* bnd;     // P + 1 chunk bounds
-    const T* la;        // N: local sub-diagonal (0 at every chunk start)
-    const T* lib;       // N: inverse pivots of the local forward sweep
-    const T* lcp;       // N: local modified super-diagonal
-    const T* v;         // N: local response to a unit value in the chunk's first row
-    const T* w;         // N: local response to a unit value in the chunk's last row
-    const T* acoup;     // P: coupling of the chunk's first row to the previous node
-    const T* ccoup;     // P: coupling of the chunk's last row to the next node
-    const T* Sinv;      // (2P)^2: inverse of the reduced system for (first, last) values
+    int N, L, implicit, periodic;
+    const T* alpha;     // L x N
+    const T* gamma;     // L x N
+    const T* ib;        // N
+    const T* z;         // N (periodic only)
+    T a0, inv_den;
 };
 
 enum { OPK_DERIV = 0, OPK_FILTER = 1, OPK_GAUSS = 2 };
@@ -73,10 +72,10 @@ struct Fields {
 
 // host-side owner of one LineTab (both precisions)
 struct HostLineTab {
-    int N = 0, P = 0, implicit = 0, periodic = 0, maxm = 0;
-    int* bnd = nullptr;
-    double* dtab = nullptr;   // 5N + 2P + 4P^2 doubles
+    int N = 0, L = 0, implicit = 0, periodic = 0;
+    double* dtab = nullptr;   // (2L + 2) N doubles: alpha, gamma, ib, z
     float* ftab = nullptr;    // same, float
+    double a0 = 0.0, inv_den = 0.0;
     size_t bytes = 0;
     double key = 0.0;         // alpha_f the table was built for (filters)
     int valid = 0;

@@ -18,290 +18,89 @@
 #include <cstdio>
 
 #include "wd_api_internal.h"
+#include "wd_pcr.cuh"
 
 namespace wd {
 
 // ------------------------------------------------------------------------------------
-// line rows
-// ------------------------------------------------------------------------------------
-
-template <typename T>
-__device__ __forceinline__ T fat(const T* F, int S, int t, int N, int per)
-{
-    if (per) {
-        if (t < 0) t += N;
-        else if (t >= N) t -= N;
-    }
-    return F[t * S];
-}
-
-// first derivative row at t (explicit value, or the right-hand side of a compact row)
-template <typename T>
-__device__ __forceinline__ T deriv_row(const T* F, int S, int t, int N, int per, int scheme)
-{
-    if (!per) {
-        if (t == 0)
-            return (T(-25.0) * F[0] + T(48.0) * F[S] - T(36.0) * F[2 * S] + T(16.0) * F[3 * S]
-                    - T(3.0) * F[4 * S]) * T(1.0 / 12.0);
-        if (t == N - 1) {
-            const T* G = F + (N - 1) * S;
-            return -(T(-25.0) * G[0] + T(48.0) * G[-S] - T(36.0) * G[-2 * S]
-                     + T(16.0) * G[-3 * S] - T(3.0) * G[-4 * S]) * T(1.0 / 12.0);
-        }
-        if (t == 1 || t == N - 2) return T(0.5) * (F[(t + 1) * S] - F[(t - 1) * S]);
-    }
-    T d1 = fat(F, S, t + 1, N, per) - fat(F, S, t - 1, N, per);
-    if (scheme == WD_E2) return T(0.5) * d1;
-    if (scheme == WD_C4) return T(0.75) * d1;
-    T d2 = fat(F, S, t + 2, N, per) - fat(F, S, t - 2, N, per);
-    if (scheme == WD_C6) return T(7.0 / 9.0) * d1 + T(1.0 / 36.0) * d2;
-    if (scheme == WD_E4 || (!per && (t == 2 || t == N - 3)))
-        return T(2.0 / 3.0) * d1 - T(1.0 / 12.0) * d2;
-    T d3 = fat(F, S, t + 3, N, per) - fat(F, S, t - 3, N, per);
-    return T(0.75) * d1 - T(0.15) * d2 + T(1.0 / 60.0) * d3;
-}
-
-// Filter right-hand side in delta form: with A fh = B f (Eq. 21) and sum_n a_n = 1 + 2 al,
-// (B - A) f = sum_{n>=1} a_n/2 (f_{t+n} + f_{t-n} - 2 f_t) - al (f_{t+1} + f_{t-1} - 2 f_t),
-// so A (fh - f) is built from second differences only; the line solve then yields the
-// correction fh - f, whose rounding error scales with the correction rather than with f
-// (the filter matrix amplifies high-frequency rounding by up to (1 + 2 al) / (1 - 2 al)).
-template <typename T>
-__device__ __forceinline__ T filter_row(const T* F, int S, int t, int N, int per, const LineOp& op)
-{
-    int hw = 5;
-    if (!per) {
-        int e = t < N - 1 - t ? t : N - 1 - t;
-        if (e < hw) hw = e;
-    }
-    if (hw == 0) return T(0);
-    const T f0 = F[t * S];
-    T s = T(0);
-    for (int m = hw; m >= 1; m--) {
-        T s2 = (fat(F, S, t + m, N, per) - f0) + (fat(F, S, t - m, N, per) - f0);
-        T cm = T(0.5 * op.fa[hw][m]) - (m == 1 ? T(op.fa[0][1]) : T(0));
-        s += cm * s2;
-    }
-    return s;
-}
-
-// truncated 9-point Gaussian (Kawai & Lele's LAD smoothing); reflection at non-periodic ends
-template <typename T>
-__device__ __forceinline__ T gauss_row(const T* F, int S, int t, int N, int per)
-{
-    const T g0 = T(3565.0 / 10368.0), g1 = T(3091.0 / 12960.0), g2 = T(1997.0 / 25920.0),
-            g3 = T(149.0 / 12960.0), g4 = T(107.0 / 103680.0);
-    const T gw[5] = {g0, g1, g2, g3, g4};
-    T s = gw[0] * F[t * S];
-#pragma unroll
-    for (int l = 1; l <= 4; l++) {
-        int ip = t + l, im = t - l;
-        if (per) {
-            if (ip >= N) ip -= N;
-            if (im < 0) im += N;
-        } else {
-            if (ip > N - 1) ip = 2 * (N - 1) - ip;
-            if (im < 0) im = -im;
-        }
-        s += gw[l] * (F[ip * S] + F[im * S]);
-    }
-    return s;
-}
-
-// ------------------------------------------------------------------------------------
-// k_line: one thread per (line, chunk).  A block holds LPB lines x P chunks (line index
-// fastest, so that for strided directions neighbouring threads read neighbouring nodes).
-// Each thread keeps its chunk (at most MAXM nodes) plus a 5-node halo in registers:
-// right-hand side, local Thomas sweep and fix-up all run in registers; only the 2P
-// chunk-end values of each line go through shared memory for the reduced system.
-// ------------------------------------------------------------------------------------
-
-constexpr int LH = 5;     // halo: E6 needs 3, the filter 5, the Gaussian 4
-constexpr int MAXM = 16;  // nodes per chunk at most (host tables guarantee it)
-
-// Row value at chunk position k (node t): the explicit derivative, the right-hand side of
-// a compact row, the delta-form filter right-hand side, or the Gaussian.  F points at the
-// register copy of node t (F[o] = node t + o).  cf[hw][m] holds the delta-form filter
-// weights a_m/2 - alpha [m == 1] of the order-2hw member.
-template <typename T>
-__device__ __forceinline__ T row_value(int kind, int sch, const T (*cf)[6], const T* F, int t,
-                                       int N, int per)
-{
-    if (kind == OPK_DERIV) {
-        if (!per) {
-            if (t == 0)
-                return (T(-25.0) * F[0] + T(48.0) * F[1] - T(36.0) * F[2] + T(16.0) * F[3]
-                        - T(3.0) * F[4]) * T(1.0 / 12.0);
-            if (t == N - 1)
-                return -(T(-25.0) * F[0] + T(48.0) * F[-1] - T(36.0) * F[-2] + T(16.0) * F[-3]
-                         - T(3.0) * F[-4]) * T(1.0 / 12.0);
-            if (t == 1 || t == N - 2) return T(0.5) * (F[1] - F[-1]);
-        }
-        T d1 = F[1] - F[-1];
-        if (sch == WD_E2) return T(0.5) * d1;
-        if (sch == WD_C4) return T(0.75) * d1;
-        T d2 = F[2] - F[-2];
-        if (sch == WD_C6) return T(7.0 / 9.0) * d1 + T(1.0 / 36.0) * d2;
-        if (sch == WD_E4 || (!per && (t == 2 || t == N - 3)))
-            return T(2.0 / 3.0) * d1 - T(1.0 / 12.0) * d2;
-        T d3 = F[3] - F[-3];
-        return T(0.75) * d1 - T(0.15) * d2 + T(1.0 / 60.0) * d3;
-    }
-    if (kind == OPK_FILTER) {
-        // delta form of Eq. 21: with sum_m a_m = 1 + 2 alpha,
-        //   A (fh - f) = sum_{m>=1} (a_m/2 - alpha [m==1]) (f_{t+m} + f_{t-m} - 2 f_t),
-        // so the line solve returns the correction fh - f, whose rounding scales with the
-        // correction instead of with f (the filter matrix amplifies high-frequency rounding
-        // by up to (1 + 2 alpha) / (1 - 2 alpha))
-        int hw = 5;
-        if (!per) {
-            int e = t < N - 1 - t ? t : N - 1 - t;
-            if (e < hw) hw = e;
-        }
-        if (hw == 0) return T(0);
-        const T f0 = F[0];
-        T s = T(0);
-#pragma unroll
-        for (int m = 5; m >= 1; m--)
-            if (m <= hw) s += cf[hw][m] * ((F[m] - f0) + (F[-m] - f0));
-        return s;
-    }
-    // truncated 9-point Gaussian (Kawai & Lele's LAD smoothing); the even reflection at
-    // non-periodic ends was applied when the halo was loaded
-    return T(3565.0 / 10368.0) * F[0] + T(3091.0 / 12960.0) * (F[1] + F[-1])
-         + T(1997.0 / 25920.0) * (F[2] + F[-2]) + T(149.0 / 12960.0) * (F[3] + F[-3])
-         + T(107.0 / 103680.0) * (F[4] + F[-4]);
-}
-
-// position loaded into halo slot t (may lie outside [0, N)): periodic wrap, even
-// reflection for the Gaussian, clamp otherwise (clamped values are never used by a row)
-__device__ __forceinline__ int halo_pos(int t, int N, int per, int reflect)
-{
-    if (per) return t < 0 ? t + N : (t >= N ? t - N : t);
-    if (reflect) return t < 0 ? -t : (t >= N ? 2 * (N - 1) - t : t);
-    return t < 0 ? 0 : (t >= N ? N - 1 : t);
-}
-
-// ------------------------------------------------------------------------------------
-// k_line: one thread per (line, chunk).  A block holds LPB lines x P chunks (line index
-// fastest, so that for strided directions neighbouring threads read neighbouring nodes).
-// Each thread keeps its chunk (at most 16 nodes) plus a 5-node halo in registers; the
-// right-hand side, the local Thomas sweep and the fix-up run in registers and only the
-// 2P chunk-end values of each line go through shared memory for the reduced system.
-// Epilogue: store each field, or accumulate out0 (+)= sum_{m<nU} xi_{dir,m} F_m and
-// out1 (+)= sum_m xi_{dir,m} F_{nU+m} (metric-weighted divergence, Eqs. 9 and 25).
+// k_line: generic line pass.  A block loads its lines into shared memory, evaluates the
+// rows (derivative, delta-form filter or Gaussian), solves the tridiagonal systems by PCR
+// (compact derivatives, filter) and either stores every field or accumulates the
+// metric-weighted divergence out0 (+)= sum_{m<nU} xi_{dir,m} F_m,
+// out1 (+)= sum_m xi_{dir,m} F_{nU+m} (Laplacian and curvature terms of Eqs. 9 and 25).
 // ------------------------------------------------------------------------------------
 
 template <typename T, typename M, int NF, int EPI, int KIND>
-__global__ void __launch_bounds__(256, 2)
+__global__ void __launch_bounds__(512)
 k_line(Dims D, int dir, int nlines, int LPB, LineTab<T> tab, LineOp op, Fields<T> f,
        const M* __restrict__ xi, int nU, int accumulate)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
-    T* Y = reinterpret_cast<T*>(smraw);              // LPB x 2P chunk-end values
     __shared__ T cf[6][6];
-    for (int i = threadIdx.x; i < 36; i += blockDim.x) {
+    const LineMap mp = make_map(D, dir, LPB, nlines, blockIdx.x * LPB);
+    const int S = mp.size();
+    T* A = reinterpret_cast<T*>(smraw);
+    T* B = A + (size_t)NF * S;
+    const int tid = threadIdx.x, nth = blockDim.x;
+    const int per = D.per[dir];
+    const long long st = D.stride(dir);
+    for (int i = tid; i < 36; i += nth) {
         int hw = i / 6, m = i % 6;
         double v = 0.0;
         if (KIND == OPK_FILTER && hw >= 1 && m >= 1 && m <= hw)
             v = 0.5 * op.fa[hw][m] - (m == 1 ? op.fa[0][1] : 0.0);
         cf[hw][m] = T(v);
     }
+    for (int s = tid; s < S; s += nth) {
+        int l, i;
+        mp.decode(s, l, i);
+        if (l >= mp.nl) continue;
+        const long long node = D.line_base(dir, mp.q0 + l) + (long long)i * st;
+#pragma unroll
+        for (int fi = 0; fi < NF; fi++) A[(size_t)fi * S + s] = f.in[fi][node];
+    }
     __syncthreads();
-    const int N = tab.N, P = tab.P, P2 = 2 * P;
-    const int l = threadIdx.x % LPB, c = threadIdx.x / LPB;
-    const int q = blockIdx.x * LPB + l;
-    const bool act = q < nlines;
-    const long long st = D.stride(dir);
-    const int per = D.per[dir];
-    constexpr int kind = KIND;
-    const int sch = op.scheme;
-    const int reflect = kind == OPK_GAUSS;
-    const long long base = act ? D.line_base(dir, q) : 0;
-    const int s = tab.bnd[c], Mc = tab.bnd[c + 1] - s;
-
-    T acc[EPI ? MAXM : 1];
-    T x[MAXM];
-
-#pragma unroll 1
-    for (int fi = 0; fi < NF; fi++) {
-        const T* __restrict__ src = f.in[fi];
-        if (act) {
-            T fr[MAXM + 2 * LH];
+    for (int s = tid; s < S; s += nth) {
+        int l, i;
+        mp.decode(s, l, i);
+        if (l >= mp.nl) continue;
 #pragma unroll
-            for (int k = 0; k < MAXM + 2 * LH; k++)
-                if (k < Mc + 2 * LH) fr[k] = src[base + (long long)halo_pos(s + k - LH, N, per, reflect) * st];
-#pragma unroll
-            for (int k = 0; k < MAXM; k++)
-                if (k < Mc) x[k] = row_value<T>(kind, sch, cf, fr + LH + k, s + k, N, per);
+        for (int fi = 0; fi < NF; fi++) {
+            const T* F = A + (size_t)fi * S;
+            T r;
+            if (KIND == OPK_DERIV) r = deriv_rhs(F, mp, l, i, per, op.scheme);
+            else if (KIND == OPK_FILTER) r = filter_rhs(F, mp, l, i, per, cf);
+            else r = gauss_rhs(F, mp, l, i, per);
+            B[(size_t)fi * S + s] = r;
         }
-        if (tab.implicit) {
-            if (act) {
-                T prev = T(0);
-#pragma unroll
-                for (int k = 0; k < MAXM; k++)
-                    if (k < Mc) {
-                        prev = (x[k] - tab.la[s + k] * prev) * tab.lib[s + k];
-                        x[k] = prev;
-                    }
-#pragma unroll
-                for (int k = MAXM - 2; k >= 0; k--)
-                    if (k < Mc - 1) x[k] = x[k] - tab.lcp[s + k] * x[k + 1];
-                T last = x[0];
-#pragma unroll
-                for (int k = 0; k < MAXM; k++)
-                    if (k == Mc - 1) last = x[k];
-                Y[l * P2 + 2 * c] = x[0];
-                Y[l * P2 + 2 * c + 1] = last;
-            }
-            __syncthreads();
-            if (act) {
-                const T ac = tab.acoup[c], cc = tab.ccoup[c];
-                const T* Yl = Y + l * P2;
-                T qm = T(0), pp = T(0);
-                if (ac != T(0)) {
-                    const T* row = tab.Sinv + (size_t)(2 * ((c - 1 + P) % P) + 1) * P2;
-                    for (int j = 0; j < P2; j++) qm += row[j] * Yl[j];
-                }
-                if (cc != T(0)) {
-                    const T* row = tab.Sinv + (size_t)(2 * ((c + 1) % P)) * P2;
-                    for (int j = 0; j < P2; j++) pp += row[j] * Yl[j];
-                }
-                const T aq = ac * qm, cp = cc * pp;
-#pragma unroll
-                for (int k = 0; k < MAXM; k++)
-                    if (k < Mc) x[k] -= aq * tab.v[s + k] + cp * tab.w[s + k];
-            }
-            __syncthreads();   // Y is reused by the next field
-        }
-        if (!act) continue;
-        if (kind == OPK_FILTER) {
-#pragma unroll
-            for (int k = 0; k < MAXM; k++)
-                if (k < Mc) x[k] += src[base + (long long)(s + k) * st];
-        }
+    }
+    __syncthreads();
+    T* X = B;
+    if (tab.implicit) X = pcr_solve<T, NF>(B, A, mp, tab);
+    for (int s = tid; s < S; s += nth) {
+        int l, i;
+        mp.decode(s, l, i);
+        if (l >= mp.nl) continue;
+        const long long node = D.line_base(dir, mp.q0 + l) + (long long)i * st;
         if (EPI == 0) {
-            T* __restrict__ dst = f.out[fi];
 #pragma unroll
-            for (int k = 0; k < MAXM; k++)
-                if (k < Mc) dst[base + (long long)(s + k) * st] = x[k];
+            for (int fi = 0; fi < NF; fi++) {
+                T v = X[(size_t)fi * S + s];
+                if (KIND == OPK_FILTER) v += f.in[fi][node];
+                f.out[fi][node] = v;
+            }
         } else {
-            const int grp = fi < nU ? 0 : 1, m = fi - grp * nU;
-            const M* __restrict__ xm = xi + (long long)(dir * 3 + m) * D.total;
-#pragma unroll
-            for (int k = 0; k < MAXM; k++)
-                if (k < Mc) {
-                    T v = T(xm[base + (long long)(s + k) * st] * M(x[k]));
-                    acc[EPI ? k : 0] = (m == 0 ? T(0) : acc[EPI ? k : 0]) + v;
-                }
-            if (m == nU - 1) {
-                T* o = f.out[grp];
-#pragma unroll
-                for (int k = 0; k < MAXM; k++)
-                    if (k < Mc) {
-                        long long p = base + (long long)(s + k) * st;
-                        o[p] = accumulate ? o[p] + acc[EPI ? k : 0] : acc[EPI ? k : 0];
-                    }
+            M s0 = M(0), s1 = M(0);
+            for (int m = 0; m < nU; m++) {
+                const M x = xi[(long long)(dir * 3 + m) * D.total + node];
+                s0 += x * M(X[(size_t)m * S + s]);
+                if (NF > nU) s1 += x * M(X[(size_t)(nU + m) * S + s]);
+            }
+            T* o0 = f.out[0];
+            o0[node] = accumulate ? T(M(o0[node]) + s0) : T(s0);
+            if (NF > nU) {
+                T* o1 = f.out[1];
+                o1[node] = accumulate ? T(M(o1[node]) + s1) : T(s1);
             }
         }
     }
@@ -312,19 +111,20 @@ static cudaError_t line_dispatch(const Dims& D, int dir, const HostLineTab& tab,
                                  const Fields<T>& f, const M* xi, int nU, int accumulate,
                                  cudaStream_t st)
 {
-    if (tab.maxm > MAXM) return cudaErrorInvalidConfiguration;
-    const int P = tab.P;
+    static int attr_done = 0;
+    if (!attr_done) {
+        cudaError_t e = cudaFuncSetAttribute(k_line<T, M, NF, EPI, KIND>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        if (e != cudaSuccess) return e;
+        attr_done = 1;
+    }
     const int nlines = D.nlines(dir);
-    // strided directions: up to 32 lines per block (coalesced rows); contiguous lines
-    // gain nothing from wide blocks.  Shrink until the grid covers the 152 SMs twice.
-    int LPB = dir == 0 ? 4 : 32;
-    while (LPB > 1 && LPB * P > 256) LPB /= 2;
-    const int min_lpb = dir == 0 ? 1 : (P <= 32 ? 8 : 2);
-    while (LPB > min_lpb && (nlines + LPB - 1) / LPB < 2 * 152) LPB /= 2;
-    if (LPB * P > 256 || LPB < 1) return cudaErrorInvalidConfiguration;
+    int LPB, threads;
+    size_t sm;
+    line_launch_shape(dir, D.n[dir], nlines, NF, sizeof(T), LPB, threads, sm);
+    if (sm > 200 * 1024) return cudaErrorInvalidConfiguration;
     int grid = (nlines + LPB - 1) / LPB;
-    size_t sm = (size_t)LPB * 2 * P * sizeof(T);
-    k_line<T, M, NF, EPI, KIND><<<grid, LPB * P, sm, st>>>(D, dir, nlines, LPB, tab.view<T>(), op, f,
+    k_line<T, M, NF, EPI, KIND><<<grid, threads, sm, st>>>(D, dir, nlines, LPB, tab.view<T>(), op, f,
                                                            xi, nU, accumulate);
     return cudaGetLastError();
 }

@@ -3,12 +3,11 @@
 // implicit filter (Sec. 3.4, Eq. 21).
 //
 // Every system has unit diagonal and constant off-diagonals except in its boundary rows,
-// and is the same for every line of a direction, so the whole solve can be factorised
-// once per (direction, scheme or alpha_f).  The GPU solves each line with the partition
-// (divide-and-conquer) method: the line is cut into P chunks, each thread runs a local
-// Thomas sweep on its chunk, and the 2P unknown chunk-end values are obtained from a
-// precomputed dense inverse of the reduced system; each chunk then adds the responses to
-// its two neighbours' end values.  All factors below are computed in double.
+// and is the same for every line of a direction, so its elimination can be prepared once
+// per (direction, scheme or alpha_f).  The GPU solves each line by parallel cyclic
+// reduction (one thread per row, log2 N levels): the multipliers of every level and the
+// final pivots depend only on the matrix and are computed here in double.  Periodic lines
+// use the Sherman-Morrison identity on top of the corner-free matrix.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -42,40 +41,6 @@ bool dense_solve(int n, std::vector<double>& M, std::vector<double>& r)
         double s = r[i];
         for (int k = i + 1; k < n; k++) s -= M[i * n + k] * r[k];
         r[i] = s / M[i * n + i];
-    }
-    return true;
-}
-
-// Inverse of an n x n matrix (row-major) by Gauss-Jordan with partial pivoting.
-static bool dense_inverse(int n, std::vector<double> A, std::vector<double>& inv)
-{
-    inv.assign((size_t)n * n, 0.0);
-    for (int i = 0; i < n; i++) inv[(size_t)i * n + i] = 1.0;
-    for (int col = 0; col < n; col++) {
-        int piv = col;
-        for (int i = col + 1; i < n; i++)
-            if (std::fabs(A[(size_t)i * n + col]) > std::fabs(A[(size_t)piv * n + col])) piv = i;
-        double p = A[(size_t)piv * n + col];
-        if (p == 0.0) return false;
-        if (piv != col)
-            for (int k = 0; k < n; k++) {
-                std::swap(A[(size_t)col * n + k], A[(size_t)piv * n + k]);
-                std::swap(inv[(size_t)col * n + k], inv[(size_t)piv * n + k]);
-            }
-        double ip = 1.0 / A[(size_t)col * n + col];
-        for (int k = 0; k < n; k++) {
-            A[(size_t)col * n + k] *= ip;
-            inv[(size_t)col * n + k] *= ip;
-        }
-        for (int i = 0; i < n; i++) {
-            if (i == col) continue;
-            double f = A[(size_t)i * n + col];
-            if (f == 0.0) continue;
-            for (int k = 0; k < n; k++) {
-                A[(size_t)i * n + k] -= f * A[(size_t)col * n + k];
-                inv[(size_t)i * n + k] -= f * inv[(size_t)col * n + k];
-            }
-        }
     }
     return true;
 }
@@ -136,89 +101,98 @@ void filter_rows(double al, int N, int periodic, std::vector<double>& a,
     }
 }
 
-// chunks per line: at most 16 nodes per chunk (the GPU keeps a chunk in registers), at
-// least 4 nodes per chunk
-int choose_chunks(int N)
+// Thomas solve of a corner-free tridiagonal system (host, double)
+static void thomas_host(int n, const std::vector<double>& a, const std::vector<double>& b,
+                        const std::vector<double>& c, const std::vector<double>& d,
+                        std::vector<double>& x)
 {
-    int P = (N + 15) / 16;
-    if (P < 1) P = 1;
-    while (P > 1 && N / P < 4) P--;
-    return P;
+    std::vector<double> cp(n), dp(n);
+    cp[0] = c[0] / b[0];
+    dp[0] = d[0] / b[0];
+    for (int i = 1; i < n; i++) {
+        double m = b[i] - a[i] * cp[i - 1];
+        cp[i] = c[i] / m;
+        dp[i] = (d[i] - a[i] * dp[i - 1]) / m;
+    }
+    x.assign(n, 0.0);
+    x[n - 1] = dp[n - 1];
+    for (int i = n - 2; i >= 0; i--) x[i] = dp[i] - cp[i] * x[i + 1];
 }
 
-// Builds the partition tables of the system with rows a_t x_{t-1} + x_t + c_t x_{t+1}
+// Builds the PCR tables of the system a_t x_{t-1} + x_t + c_t x_{t+1} = d_t
 // (periodic: a_0 couples x_{N-1} and c_{N-1} couples x_0).
-wd_status build_line_table(int N, int periodic, const std::vector<double>& a,
-                           const std::vector<double>& c, int implicit, HostLineTab& tab)
+wd_status build_line_table(int N, int periodic, const std::vector<double>& a0v,
+                           const std::vector<double>& c0v, int implicit, HostLineTab& tab)
 {
     free_line_table(tab);
-    int P = choose_chunks(N);
     tab.N = N;
-    tab.P = P;
     tab.implicit = implicit;
     tab.periodic = periodic;
-    std::vector<int> bnd(P + 1);
-    for (int ch = 0; ch <= P; ch++) bnd[ch] = (int)((long long)ch * N / P);
-    tab.maxm = 0;
-    for (int ch = 0; ch < P; ch++) tab.maxm = std::max(tab.maxm, bnd[ch + 1] - bnd[ch]);
-    if (tab.maxm > 16) return set_error(WD_ERR_INVALID_ARG, "line chunk longer than 16 nodes");
-    size_t nd = (size_t)5 * N + 2 * P + (size_t)4 * P * P;
-    std::vector<double> h(nd, 0.0);
-    double *la = h.data(), *lib = la + N, *lcp = lib + N, *v = lcp + N, *w = v + N;
-    double *acoup = w + N, *ccoup = acoup + P, *Sinv = ccoup + P;
-    if (implicit) {
-        for (int ch = 0; ch < P; ch++) {
-            int s = bnd[ch], e = bnd[ch + 1];
-            for (int t = s; t < e; t++) {
-                la[t] = (t == s) ? 0.0 : a[t];
-                double den = 1.0 - ((t == s) ? 0.0 : a[t] * lcp[t - 1]);
-                lib[t] = 1.0 / den;
-                lcp[t] = (t < e - 1) ? c[t] * lib[t] : 0.0;
-            }
-            // responses to unit values in the first and the last row of the chunk
-            for (int which = 0; which < 2; which++) {
-                double* out = which == 0 ? v : w;
-                double prev = 0.0;
-                for (int t = s; t < e; t++) {
-                    double d = (which == 0 ? (t == s) : (t == e - 1)) ? 1.0 : 0.0;
-                    prev = (d - la[t] * prev) * lib[t];
-                    out[t] = prev;
-                }
-                double next = out[e - 1];
-                for (int t = e - 2; t >= s; t--) {
-                    next = out[t] - lcp[t] * next;
-                    out[t] = next;
-                }
-            }
-            acoup[ch] = a[s];
-            ccoup[ch] = c[e - 1];
-        }
-        int n2 = 2 * P;
-        std::vector<double> S((size_t)n2 * n2, 0.0), Si;
-        for (int i = 0; i < n2; i++) S[(size_t)i * n2 + i] = 1.0;
-        for (int ch = 0; ch < P; ch++) {
-            int s = bnd[ch], e = bnd[ch + 1];
-            int prev = (ch - 1 + P) % P, next = (ch + 1) % P;
-            S[(size_t)(2 * ch) * n2 + 2 * prev + 1] += acoup[ch] * v[s];
-            S[(size_t)(2 * ch) * n2 + 2 * next] += ccoup[ch] * w[s];
-            S[(size_t)(2 * ch + 1) * n2 + 2 * prev + 1] += acoup[ch] * v[e - 1];
-            S[(size_t)(2 * ch + 1) * n2 + 2 * next] += ccoup[ch] * w[e - 1];
-        }
-        if (!dense_inverse(n2, S, Si)) return set_error(WD_ERR_INVALID_ARG, "singular line system");
-        std::memcpy(Sinv, Si.data(), sizeof(double) * n2 * n2);
+    std::vector<double> a = a0v, b(N, 1.0), c = c0v;
+    if (periodic) {
+        // B = A - u v^T with u = (-1, 0, .., 0, c_{N-1}), v = (1, 0, .., 0, -a_0): corner-free,
+        // diagonal changed in its first and last entries
+        b[0] = 2.0;
+        b[N - 1] = 1.0 + a[0] * c[N - 1];
+        tab.a0 = a[0];
     }
+    a[0] = 0.0;
+    c[N - 1] = 0.0;
+    std::vector<double> z(N, 0.0);
+    if (periodic && implicit) {
+        std::vector<double> u(N, 0.0);
+        u[0] = -1.0;
+        u[N - 1] = c0v[N - 1];
+        thomas_host(N, a, b, c, u, z);
+        tab.inv_den = 1.0 / (1.0 + z[0] - tab.a0 * z[N - 1]);
+    }
+    int L = 0;
+    while ((1 << L) < N) L++;
+    tab.L = implicit ? L : 0;
+    std::vector<double> h((size_t)(2 * L + 2) * N, 0.0);
+    double* alpha = h.data();
+    double* gamma = alpha + (size_t)L * N;
+    double* ib = gamma + (size_t)L * N;
+    double* zt = ib + N;
+    if (implicit) {
+        for (int lev = 0; lev < L; lev++) {
+            int hh = 1 << lev;
+            std::vector<double> na(N, 0.0), nb = b, nc(N, 0.0);
+            for (int i = 0; i < N; i++) {
+                double al = 0.0, ga = 0.0;
+                if (i - hh >= 0) {
+                    al = -a[i] / b[i - hh];
+                    na[i] = al * a[i - hh];
+                    nb[i] += al * c[i - hh];
+                }
+                if (i + hh < N) {
+                    ga = -c[i] / b[i + hh];
+                    nc[i] = ga * c[i + hh];
+                    nb[i] += ga * a[i + hh];
+                }
+                alpha[(size_t)lev * N + i] = al;
+                gamma[(size_t)lev * N + i] = ga;
+            }
+            a = na;
+            b = nb;
+            c = nc;
+        }
+    }
+    for (int i = 0; i < N; i++) {
+        ib[i] = implicit ? 1.0 / b[i] : 1.0;
+        zt[i] = z[i];
+    }
+    size_t nd = h.size();
     std::vector<float> hf(nd);
     for (size_t i = 0; i < nd; i++) hf[i] = (float)h[i];
-    tab.bytes = nd * (sizeof(double) + sizeof(float)) + (P + 1) * sizeof(int);
-    if (cudaMalloc(&tab.bnd, (P + 1) * sizeof(int)) != cudaSuccess ||
-        cudaMalloc(&tab.dtab, nd * sizeof(double)) != cudaSuccess ||
+    tab.bytes = nd * (sizeof(double) + sizeof(float));
+    if (cudaMalloc(&tab.dtab, nd * sizeof(double)) != cudaSuccess ||
         cudaMalloc(&tab.ftab, nd * sizeof(float)) != cudaSuccess) {
         free_line_table(tab);
         cudaGetLastError();
         return set_error(WD_ERR_OOM, "cudaMalloc of a line-solve table failed");
     }
-    if (cudaMemcpy(tab.bnd, bnd.data(), (P + 1) * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(tab.dtab, h.data(), nd * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
+    if (cudaMemcpy(tab.dtab, h.data(), nd * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(tab.ftab, hf.data(), nd * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess) {
         free_line_table(tab);
         return set_error(WD_ERR_CUDA, "upload of a line-solve table failed");
@@ -229,10 +203,8 @@ wd_status build_line_table(int N, int periodic, const std::vector<double>& a,
 
 void free_line_table(HostLineTab& tab)
 {
-    if (tab.bnd) cudaFree(tab.bnd);
     if (tab.dtab) cudaFree(tab.dtab);
     if (tab.ftab) cudaFree(tab.ftab);
-    tab.bnd = nullptr;
     tab.dtab = nullptr;
     tab.ftab = nullptr;
     tab.valid = 0;
@@ -243,20 +215,17 @@ template <typename T>
 static LineTab<T> make_view(const HostLineTab& h, const T* base)
 {
     LineTab<T> t;
-    int N = h.N, P = h.P;
+    int N = h.N, L = h.L;
     t.N = N;
-    t.P = P;
+    t.L = L;
     t.implicit = h.implicit;
-    t.periodic = h.periodic;
-    t.bnd = h.bnd;
-    t.la = base;
-    t.lib = base + N;
-    t.lcp = base + 2 * N;
-    t.v = base + 3 * N;
-    t.w = base + 4 * N;
-    t.acoup = base + 5 * N;
-    t.ccoup = base + 5 * N + P;
-    t.Sinv = base + 5 * N + 2 * P;
+    t.periodic = h.periodic && h.implicit;
+    t.alpha = base;
+    t.gamma = base + (size_t)L * N;
+    t.ib = base + (size_t)2 * L * N;
+    t.z = base + (size_t)(2 * L + 1) * N;
+    t.a0 = T(h.a0);
+    t.inv_den = T(h.inv_den);
     return t;
 }
 

@@ -221,3 +221,25 @@ def test_full_solve(wd, oracle, case):
     assert st["converged"], st
     err = np.abs(to_np(out) - ref).max()
     assert err <= tol * spec.L_ref, (name, err, st, ost)
+
+
+GENERIC_CASES = [0, 2, 4, 5]   # 2-D cases of STEP_CASES
+
+
+@pytest.mark.parametrize("case", GENERIC_CASES)
+def test_pseudo_steps_generic_path(wd, oracle, case, monkeypatch):
+    """2-D grids normally take the fused pseudo step; WD_FORCE_GENERIC=1 at grid creation
+    selects the generic kernel sequence, which must agree with the oracle as well."""
+    monkeypatch.setenv("WD_FORCE_GENERIC", "1")
+    gname, scheme, kw = STEP_CASES[case]
+    spec = GRIDS[gname]()
+    prm = base_params(scheme, **kw)
+    og = oracle_grid(oracle, spec, scheme)
+    g = wd.Grid(spec, 0, scheme)
+    ex = exact_of(spec)
+    if ex is None:
+        ex = np.hypot(*spec.xyz) - 0.5
+    phi0 = og.apply_bc(ex + 0.02 * W.random_field(spec, 11))
+    ref, _ = og.hj_steps(phi0, 4, **oracle_kw(scheme, prm))
+    out, _ = g.steps(gpu_params(wd, scheme, prm), g.as_field(phi0), 4, kind=0)
+    np.testing.assert_allclose(to_np(out), ref, atol=1e-10 * scale(ref), rtol=0)
