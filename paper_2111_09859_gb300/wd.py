@@ -84,6 +84,7 @@ SIGNATURES = {
     "wd_steps": (_i, [_vp, C.POINTER(SolveParams), _i, _vp, _i, C.POINTER(Stats)]),
     "wd_profile": (_i, [_vp, _i]),
     "wd_profile_read": (_i, [_vp, _i, C.POINTER(C.c_double), C.POINTER(C.c_longlong)]),
+    "wd_change_norms_noalloc": (_i, [_vp, _vp, _vp, C.c_longlong, _i, _d, _vp, _vp]),
 }
 
 K_DERIV, K_DIV, K_FILTER, K_GAUSS, K_POINT, K_BC, K_NORM = range(7)
@@ -309,3 +310,15 @@ def footprint(spec, precision=FP64, scheme=E4):
     d.scheme = scheme
     d.L_ref = 1.0
     return lib().wd_query_footprint(C.byref(d), None)
+
+
+def change_norms_noalloc(new, old, mask=None, scale=1.0, stream=None):
+    """RMS and max of new - old over entries with mask == 0, through the allocation-free
+    entry point; returns a device tensor of 2 doubles (enqueued on the stream)."""
+    import torch
+
+    prec = FP64 if new.dtype == torch.float64 else FP32
+    out = torch.empty(2, dtype=torch.float64, device=new.device)
+    _check(lib().wd_change_norms_noalloc(_ptr(new), _ptr(old), _ptr(mask), new.numel(), prec,
+                                         float(scale), _ptr(out), _stream_handle(stream)))
+    return out
