@@ -3,12 +3,14 @@
 
 A step = one complete wall-distance solve of the workload: Poisson initial guess, HJ
 pseudo-time marching (RK4, local time steps, filter, change norms) until the tolerance.
-Default workload: the O-grid around a circular cylinder (257 radial x 512 periodic
-circumferential nodes, wall radius 0.5, outer radius 10, radial ratio 1.03), compact C6
-scheme, LAD pseudo-HJ with the curvature correction, alpha_f = 0.495, FP32 state with FP64
-metrics, tolerance RMS(dphi) <= 1e-6 L.  Metric: Mcell-iter/s = nodes x pseudo steps /
-device time.  Every rank solves its own copies (weak scaling, no collective on the data
-path); rank 0 prints one JSON line.
+Workload (the cylinder case): O-grids around circular cylinders, 257 radial x 512 periodic
+circumferential nodes, outer radius 10, radial ratio 1.03, compact C6 scheme, LAD
+pseudo-HJ with the curvature correction, alpha_f = 0.495.  The timed form is FP32 state
+with FP64 metrics, BATCH cylinders stacked in one grid object (wall radii 0.5 (1 + k/100)),
+tolerance RMS(dphi) <= 1e-6 per cylinder; the FP64 plain form (one cylinder, tolerance
+1e-10) is timed once beside it.  Metric: Mcell-iter/s = cylinders x nodes x pseudo steps /
+device time.  Ranks solve their own batches (weak scaling, no collective on the data path);
+rank 0 prints one JSON line.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
 """
@@ -29,10 +31,14 @@ METRIC = "Mcell-iter/s & time-to-converged d (FP32 batched vs FP64 plain), p99 l
 UNIT = "Mcell-iter/s"
 
 
-def workload_spec():
+BATCH = 16
+
+
+def workload_spec(batch=1):
     from paper_2111_09859_gb300 import workloads as W
 
-    return W.cylinder(257, 512, 1.03)
+    members = [W.cylinder(257, 512, 1.03, r_wall=0.5 * (1 + 0.01 * k)) for k in range(batch)]
+    return W.stack(members) if batch > 1 else members[0]
 
 
 def solve_params(wd, tol):
@@ -133,7 +139,8 @@ def run_native(args, rank, world):
     B.build()
     from paper_2111_09859_gb300 import wd
 
-    spec = workload_spec()
+    spec = workload_spec(BATCH)
+    single = workload_spec(1)
     prec = wd.FP32_METRIC64
     tol = 1e-6
     p = solve_params(wd, tol)
@@ -194,14 +201,17 @@ def run_native(args, rank, world):
     cell_iters = nodes * (iters + piters) * world
     value = cell_iters / (ms * 1e-3) / 1e6
 
-    # accuracy of the timed result against the exact distance r - 0.5
+    # accuracy of the timed result against the exact distance r - r_wall of every cylinder
     import numpy as np
 
-    exact = np.hypot(*spec.xyz) - 0.5
-    err32 = float(np.abs(phi.double().cpu().numpy() - exact).max())
+    n1 = single.N
+    rw = np.repeat([0.5 * (1 + 0.01 * k) for k in range(BATCH)], n1)
+    exact = np.hypot(*spec.xyz) - rw
+    phi_np = phi.double().cpu().numpy()
+    err32 = float(np.abs(phi_np - exact).max())
 
-    # FP64 plain form on the same grid: time-to-converged at tolerance 1e-10
-    g64 = wd.Grid(spec, wd.FP64, wd.C6, stream=stream)
+    # FP64 plain form on one cylinder (r_wall 0.5): time-to-converged at tolerance 1e-10
+    g64 = wd.Grid(single, wd.FP64, wd.C6, stream=stream)
     phi64 = g64.empty()
     p64 = solve_params(wd, 1e-10)
     g64.solve(p64, phi64)
@@ -212,13 +222,13 @@ def run_native(args, rank, world):
     ev1.record(stream)
     torch.cuda.synchronize()
     t64 = ev0.elapsed_time(ev1) * 1e-3
-    err64 = float(np.abs(phi64.cpu().numpy() - exact).max())
-    diff = float(np.abs(phi64.cpu().numpy() - phi.double().cpu().numpy()).max())
+    err64 = float(np.abs(phi64.cpu().numpy() - exact[:n1]).max())
+    diff = float(np.abs(phi64.cpu().numpy() - phi_np[:n1]).max())
     del g64
 
     # end to end through the public API with host buffers: grid creation from host
     # coordinates (H2D), solve, result copied to pinned host memory (D2H)
-    host_phi = torch.empty(nodes, dtype=torch.float32).pin_memory()
+    host_phi = torch.empty(nodes, dtype=torch.float32).pin_memory()   # whole batch
     e2e_ms = 0.0
     for _ in range(args.steps):
         torch.cuda.synchronize()
@@ -251,13 +261,15 @@ def run_native(args, rank, world):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32 (metrics f64)",
         "data": "synthetic",
-        "config": {"workload": "cylinder O-grid 257x512 (r 0.5..10, ratio 1.03), C6 + LAD + curvature, "
-                               "alpha_f 0.495, FP32 state / FP64 metrics, tol RMS 1e-6, Poisson 100",
-                   "nodes": nodes, "pseudo_steps_per_solve": (iters + piters) / args.steps,
+        "config": {"workload": f"{BATCH} stacked cylinder O-grids 257x512 (r_wall 0.5(1+k/100), "
+                               "r_out 10, ratio 1.03), C6 + LAD + curvature, alpha_f 0.495, "
+                               "FP32 state / FP64 metrics, tol RMS 1e-6 per cylinder, Poisson 100",
+                   "batch": BATCH, "nodes": nodes, "pseudo_steps_per_solve": (iters + piters) / args.steps,
                    "l2_between_steps": "flushed (256 MB write)",
                    "parallelism": f"replicas x{world}"},
-        "time_to_converged_s": {"fp32_metric64": round(ms / args.steps * 1e-3, 4),
-                                "fp64_plain": round(t64, 4), "fp64_iters": st64["iters"]},
+        "time_to_converged_s": {"fp32_batched_per_cylinder": round(ms / args.steps * 1e-3 / BATCH, 4),
+                                "fp32_batch_of_%d" % BATCH: round(ms / args.steps * 1e-3, 4),
+                                "fp64_plain_one_cylinder": round(t64, 4), "fp64_iters": st64["iters"]},
         "accuracy": {"max_err_vs_exact_fp32m64": err32, "max_err_vs_exact_fp64": err64,
                      "max_fp32_minus_fp64": diff},
         "roofline": roof,
@@ -265,7 +277,8 @@ def run_native(args, rank, world):
         "gpu_launches": int(launches),
         "clocks": clk,
         "e2e": {"value": round(e2e_value, 2) if e2e_value else None, "unit": UNIT,
-                "h2d_bytes_per_step": int(spec.xyz.nbytes), "d2h_bytes_per_step": int(nodes * 4)},
+                "h2d_bytes_per_step": int(spec.xyz.nbytes), "d2h_bytes_per_step": int(nodes * 4),
+                "what": "wd_create_grid from host coordinates + wd_solve into pinned host memory + destroy"},
     }
     if rank == 0:
         out["cpu_baseline"] = cpu_baseline()
@@ -283,7 +296,7 @@ def cpu_baseline(n_steps=12):
 
     import oracle as O
 
-    spec = workload_spec()
+    spec = workload_spec(1)
     og = O.Grid(spec.shape, spec.xyz, spec.bc_lo, spec.bc_hi, scheme=O.C6, period=spec.period)
     kw = dict(equation=O.HJ_LAD, scheme=O.C6, curvature=1, alpha_f=0.495, cfl=0.6)
     phi0 = og.apply_bc(np.hypot(*spec.xyz) - 0.5)
@@ -303,7 +316,7 @@ def run_reference(args, rank, world):
     import oracle as O
 
     O.build()
-    spec = workload_spec()
+    spec = workload_spec(1)
     og = O.Grid(spec.shape, spec.xyz, spec.bc_lo, spec.bc_hi, scheme=O.C6, period=spec.period)
     kw = dict(equation=O.HJ_LAD, scheme=O.C6, curvature=1, alpha_f=0.495, cfl=0.6)
     phi = og.apply_bc(np.hypot(*spec.xyz) - 0.5)

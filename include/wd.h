@@ -5,8 +5,11 @@
  * wall distance computations" (arXiv 2111.09859).
  *
  * Conventions shared by every entry point
- *  - A grid has n[0] x n[1] x n[2] nodes (n[2] = 1 in 2-D).  Node (i, j, k) of every
- *    caller array sits at i + n[0] * (j + n[1] * k) (dense, i fastest).
+ *  - A grid has n[0] x n[1] x n[2] nodes.  Node (i, j, k) of every caller array sits at
+ *    i + n[0] * (j + n[1] * k) (dense, i fastest).  In 2-D, n[2] > 1 stacks n[2]
+ *    independent grids of n[0] x n[1] nodes (grid k holds the nodes with that k; same
+ *    boundary kinds, own coordinates, masks and convergence norms); they are solved
+ *    together by the same launches, and stats report the worst of them.
  *  - "phi" arrays hold the grid's state precision: double for WD_FP64, float for
  *    WD_FP32_METRIC64 and WD_FP32.  Metric exports are always double.
  *  - Pointers named *_dev are CUDA device pointers owned by the caller; *_host are host
@@ -73,7 +76,9 @@ enum { WD_INIT_ZERO = 0,     /* phi = 0 (Sec. 3.5) */
 
 typedef struct {
     int ndim;              /* 2 or 3 */
-    int n[3];              /* nodes per direction, each >= 8 for d < ndim; n[2] = 1 in 2-D */
+    int n[3];              /* nodes per direction, each >= 8 for d < ndim; in 2-D n[2] is the
+                              number of stacked grids (1 for a single grid; > 1 needs
+                              periodic or wall faces in direction 0) */
     int bc_lo[3];          /* WD_BC_* of the face at index 0 of each direction */
     int bc_hi[3];          /* WD_BC_* of the face at index n-1 of each direction */
     double period[3][3];   /* periodic direction d: x(i + n[d]) = x(i) + period[d] */

@@ -70,6 +70,8 @@ struct wd_grid_s {
     uint8_t* mask = nullptr;
     void* dval = nullptr;
     long long nactive = 0;
+    int batch = 1;                       // stacked 2-D grids (n[2] in 2-D)
+    std::vector<long long> nact;         // active nodes per stacked grid
     void* w[W_NWORK] = {};
     double* partial = nullptr;
     unsigned* counter = nullptr;
@@ -171,7 +173,7 @@ static size_t footprint_bytes(const wd_grid_desc* d)
     for (int k = 0; k < d->ndim; k++) {
         int L = 0;
         while ((1 << L) < d->n[k]) L++;
-        b += 3 * (size_t)(2 * L + 2) * d->n[k] * 12;
+        b += 3 * (size_t)(2 * L + 3) * d->n[k] * 12;
     }
     return b;
 }
@@ -180,7 +182,13 @@ static wd_status validate_desc(const wd_grid_desc* d)
 {
     if (!d) return set_error(WD_ERR_INVALID_ARG, "desc is NULL");
     if (d->ndim != 2 && d->ndim != 3) return set_error(WD_ERR_INVALID_ARG, "ndim must be 2 or 3");
-    if (d->ndim == 2 && d->n[2] != 1) return set_error(WD_ERR_INVALID_ARG, "n[2] must be 1 in 2-D");
+    if (d->n[2] < 1) return set_error(WD_ERR_INVALID_ARG, "n[2] must be >= 1 (grids stacked in 2-D)");
+    if (d->ndim == 2 && d->n[2] > 1) {
+        auto ok = [](int k) { return k == WD_BC_PERIODIC || k == WD_BC_WALL; };
+        if (!ok(d->bc_lo[0]) || !ok(d->bc_hi[0]))
+            return set_error(WD_ERR_INVALID_ARG,
+                             "stacked 2-D grids need periodic or wall faces in direction 0");
+    }
     for (int k = 0; k < d->ndim; k++) {
         if (d->n[k] < 8) return set_error(WD_ERR_INVALID_ARG, "every direction needs >= 8 nodes");
         if (d->n[k] > 2048) return set_error(WD_ERR_INVALID_ARG, "at most 2048 nodes per direction");
@@ -506,6 +514,7 @@ struct Solver {
         a.counter = g->counter;
         a.result = g->result;
         a.max_partials = g->npartial;
+        a.batch = g->batch;
         return a;
     }
 
@@ -548,6 +557,7 @@ struct Solver {
     wd_status step(bool poisson)
     {
         if (fused2d()) return step_fused(poisson);
+        if (g->batch > 1) return set_error(WD_ERR_INVALID_ARG, "stacked 2-D grids need the fused path");
         for (int s = 0; s < 4; s++) {
             const T* src = s == 0 ? W(W_PHIN) : W(W_PHIS);
             ST(rhs_into(src, W(W_PHIS), poisson, s));
@@ -604,13 +614,22 @@ struct Solver {
         return WD_OK;
     }
 
+    // change norms of the last pseudo step; stacked grids report their worst member
     wd_status read_norms(double scale, double* l2, double* linf)
     {
-        CK(cudaMemcpyAsync(g->hres, g->result, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+        const int B = g->batch;
+        CK(cudaMemcpyAsync(g->hres, g->result, (size_t)2 * B * sizeof(double), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
-        double n = g->nactive > 0 ? (double)g->nactive : 1.0;
-        *l2 = std::sqrt(g->hres[0] / n) / scale;
-        *linf = g->hres[1] / scale;
+        double a = 0.0, b = 0.0;
+        for (int k = 0; k < B; k++) {
+            const double n = g->nact[k] > 0 ? (double)g->nact[k] : 1.0;
+            const double l = std::sqrt(g->hres[2 * k] / n) / scale;
+            const double m = g->hres[2 * k + 1] / scale;
+            if (!(l <= a)) a = l;   // keeps NaN
+            if (!(m <= b)) b = m;
+        }
+        *l2 = a;
+        *linf = b;
         return WD_OK;
     }
 
@@ -903,25 +922,38 @@ static wd_status create_impl(wd_grid g, const double* xyz_host, const uint8_t* m
         CK(cudaMemsetAsync(g->w[k], 0, (size_t)tot * sizeof(T), st));
     }
     g->nred = (int)std::min<long long>((tot + 255) / 256, 1024);
-    g->npartial = std::max(g->nred, std::max(D.n[0], D.n[1] * (D.ndim == 3 ? D.n[2] : 1)));
+    g->npartial = std::max(g->nred, D.n[0] * D.n[2]);
     ST(dmalloc(g, (void**)&g->partial, (size_t)g->npartial * 2 * 8));
     ST(dmalloc(g, (void**)&g->counter, sizeof(unsigned)));
-    ST(dmalloc(g, (void**)&g->result, 2 * 8));
+    ST(dmalloc(g, (void**)&g->result, (size_t)2 * g->batch * 8));
     CK(cudaMemsetAsync(g->counter, 0, sizeof(unsigned), st));
-    CK(cudaMemsetAsync(g->result, 0, 2 * 8, st));
-    if (cudaMallocHost(&g->hres, 2 * sizeof(double)) != cudaSuccess) return set_error(WD_ERR_OOM, "pinned");
+    CK(cudaMemsetAsync(g->result, 0, (size_t)2 * g->batch * 8, st));
+    if (cudaMallocHost(&g->hres, (size_t)2 * g->batch * sizeof(double)) != cudaSuccess)
+        return set_error(WD_ERR_OOM, "pinned");
     CK(cudaStreamSynchronize(st));
     return WD_OK;
 }
 
 static wd_status count_active(wd_grid g)
 {
-    CK(cudaMemsetAsync(g->dcount, 0, sizeof(unsigned long long), g->stream));
-    CK(launch_count(g->D, g->mask, g->dcount, g->stream));
-    unsigned long long c = 0;
-    CK(cudaMemcpyAsync(&c, g->dcount, sizeof(c), cudaMemcpyDeviceToHost, g->stream));
-    CK(cudaStreamSynchronize(g->stream));
-    g->nactive = (long long)c;
+    // stacked 2-D grids are contiguous blocks of pitch * n[1] elements
+    Dims one = g->D;
+    const int B = g->batch;
+    if (B > 1) {
+        one.n[2] = 1;
+        one.total = (long long)one.pitch * one.n[1];
+    }
+    g->nact.assign(B, 0);
+    g->nactive = 0;
+    for (int k = 0; k < B; k++) {
+        CK(cudaMemsetAsync(g->dcount, 0, sizeof(unsigned long long), g->stream));
+        CK(launch_count(one, g->mask + (long long)k * one.total, g->dcount, g->stream));
+        unsigned long long c = 0;
+        CK(cudaMemcpyAsync(&c, g->dcount, sizeof(c), cudaMemcpyDeviceToHost, g->stream));
+        CK(cudaStreamSynchronize(g->stream));
+        g->nact[k] = (long long)c;
+        g->nactive += (long long)c;
+    }
     return WD_OK;
 }
 
@@ -975,6 +1007,7 @@ wd_status wd_create_grid(const wd_grid_desc* desc, const double* xyz_host, const
     }
     D.pitch = (desc->n[0] + 31) / 32 * 32;
     D.total = (long long)D.pitch * D.n[1] * D.n[2];
+    g->batch = desc->ndim == 2 ? desc->n[2] : 1;
     {
         const char* fg = std::getenv("WD_FORCE_GENERIC");
         g->force_generic = fg && fg[0] == '1';

@@ -38,6 +38,7 @@ struct F2Args {
     unsigned* counter;
     double* result;                      // sum of squares, max |change|
     int max_partials;
+    int batch;                           // stacked grids (n[2]); result holds 2 per grid
     int lpb[3], nb[3];                   // filled by the launcher
 };
 

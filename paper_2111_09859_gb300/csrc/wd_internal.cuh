@@ -73,7 +73,10 @@ struct Fields {
 // host-side owner of one LineTab (both precisions)
 struct HostLineTab {
     int N = 0, L = 0, implicit = 0, periodic = 0;
-    double* dtab = nullptr;   // (2L + 2) N doubles: alpha, gamma, ib, z
+    int L64 = 0, L32 = 0;     // levels after which the remaining coupling is below double /
+                              // float rounding (L64 <= L, L32 <= L64)
+    double* dtab = nullptr;   // (2L + 3) N doubles: alpha, gamma, ib (after L64 levels),
+                              // ib (after L32 levels), z
     float* ftab = nullptr;    // same, float
     double a0 = 0.0, inv_den = 0.0;
     size_t bytes = 0;

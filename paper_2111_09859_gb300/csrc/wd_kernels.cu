@@ -30,7 +30,7 @@ namespace wd {
 // out1 (+)= sum_m xi_{dir,m} F_{nU+m} (Laplacian and curvature terms of Eqs. 9 and 25).
 // ------------------------------------------------------------------------------------
 
-template <typename T, typename M, int NF, int EPI, int KIND>
+template <typename T, typename M, int NF, int EPI, int KIND, int R>
 __global__ void __launch_bounds__(512)
 k_line(Dims D, int dir, int nlines, int LPB, LineTab<T> tab, LineOp op, Fields<T> f,
        const M* __restrict__ xi, int nU, int accumulate)
@@ -41,51 +41,48 @@ k_line(Dims D, int dir, int nlines, int LPB, LineTab<T> tab, LineOp op, Fields<T
     const int S = mp.size();
     T* A = reinterpret_cast<T*>(smraw);
     T* B = A + (size_t)NF * S;
-    const int tid = threadIdx.x, nth = blockDim.x;
     const int per = D.per[dir];
-    const long long st = D.stride(dir);
-    for (int i = tid; i < 36; i += nth) {
-        int hw = i / 6, m = i % 6;
-        double v = 0.0;
-        if (KIND == OPK_FILTER && hw >= 1 && m >= 1 && m <= hw)
-            v = 0.5 * op.fa[hw][m] - (m == 1 ? op.fa[0][1] : 0.0);
-        cf[hw][m] = T(v);
-    }
-    for (int s = tid; s < S; s += nth) {
-        int l, i;
-        mp.decode(s, l, i);
-        if (l >= mp.nl) continue;
-        const long long node = D.line_base(dir, mp.q0 + l) + (long long)i * st;
+    Slot q[R];
+    slots_init<R>(q, mp, D);
+    if (KIND == OPK_FILTER)
+        for (int i = threadIdx.x; i < 36; i += blockDim.x) {
+            const int hw = i / 6, m = i % 6;
+            double v = 0.0;
+            if (hw >= 1 && m >= 1 && m <= hw) v = 0.5 * op.fa[hw][m] - (m == 1 ? op.fa[0][1] : 0.0);
+            cf[hw][m] = T(v);
+        }
 #pragma unroll
-        for (int fi = 0; fi < NF; fi++) A[(size_t)fi * S + s] = f.in[fi][node];
+    for (int r = 0; r < R; r++) {
+        if (q[r].s < 0) continue;
+#pragma unroll
+        for (int fi = 0; fi < NF; fi++) A[(size_t)fi * S + q[r].s] = f.in[fi][q[r].node];
     }
     __syncthreads();
-    for (int s = tid; s < S; s += nth) {
-        int l, i;
-        mp.decode(s, l, i);
-        if (l >= mp.nl) continue;
+#pragma unroll
+    for (int r = 0; r < R; r++) {
+        if (q[r].s < 0) continue;
 #pragma unroll
         for (int fi = 0; fi < NF; fi++) {
-            const T* F = A + (size_t)fi * S;
-            T r;
-            if (KIND == OPK_DERIV) r = deriv_rhs(F, mp, l, i, per, op.scheme);
-            else if (KIND == OPK_FILTER) r = filter_rhs(F, mp, l, i, per, cf);
-            else r = gauss_rhs(F, mp, l, i, per);
-            B[(size_t)fi * S + s] = r;
+            const LineView<T> v = view_of<T>(A + (size_t)fi * S, q[r], mp, per);
+            T x;
+            if (KIND == OPK_DERIV) x = deriv_rhs(v, q[r].i, op.scheme);
+            else if (KIND == OPK_FILTER) x = filter_rhs(v, q[r].i, cf);
+            else x = gauss_rhs(v, q[r].i);
+            B[(size_t)fi * S + q[r].s] = x;
         }
     }
     __syncthreads();
     T* X = B;
-    if (tab.implicit) X = pcr_solve<T, NF>(B, A, mp, tab);
-    for (int s = tid; s < S; s += nth) {
-        int l, i;
-        mp.decode(s, l, i);
-        if (l >= mp.nl) continue;
-        const long long node = D.line_base(dir, mp.q0 + l) + (long long)i * st;
+    if (tab.implicit) X = pcr_solve<T, NF, R>(B, A, mp, tab, q);
+#pragma unroll
+    for (int r = 0; r < R; r++) {
+        const int sl = q[r].s;
+        if (sl < 0) continue;
+        const long long node = q[r].node;
         if (EPI == 0) {
 #pragma unroll
             for (int fi = 0; fi < NF; fi++) {
-                T v = X[(size_t)fi * S + s];
+                T v = X[(size_t)fi * S + sl];
                 if (KIND == OPK_FILTER) v += f.in[fi][node];
                 f.out[fi][node] = v;
             }
@@ -93,8 +90,8 @@ k_line(Dims D, int dir, int nlines, int LPB, LineTab<T> tab, LineOp op, Fields<T
             M s0 = M(0), s1 = M(0);
             for (int m = 0; m < nU; m++) {
                 const M x = xi[(long long)(dir * 3 + m) * D.total + node];
-                s0 += x * M(X[(size_t)m * S + s]);
-                if (NF > nU) s1 += x * M(X[(size_t)(nU + m) * S + s]);
+                s0 += x * M(X[(size_t)m * S + sl]);
+                if (NF > nU) s1 += x * M(X[(size_t)(nU + m) * S + sl]);
             }
             T* o0 = f.out[0];
             o0[node] = accumulate ? T(M(o0[node]) + s0) : T(s0);
@@ -106,27 +103,40 @@ k_line(Dims D, int dir, int nlines, int LPB, LineTab<T> tab, LineOp op, Fields<T
     }
 }
 
-template <typename T, typename M, int NF, int EPI, int KIND>
-static cudaError_t line_dispatch(const Dims& D, int dir, const HostLineTab& tab, const LineOp& op,
-                                 const Fields<T>& f, const M* xi, int nU, int accumulate,
-                                 cudaStream_t st)
+template <typename T, typename M, int NF, int EPI, int KIND, int R>
+static cudaError_t line_dispatch_r(const Dims& D, int dir, const HostLineTab& tab, const LineOp& op,
+                                   const Fields<T>& f, const M* xi, int nU, int accumulate,
+                                   cudaStream_t st, int LPB, int threads, size_t sm)
 {
     static int attr_done = 0;
     if (!attr_done) {
-        cudaError_t e = cudaFuncSetAttribute(k_line<T, M, NF, EPI, KIND>,
+        cudaError_t e = cudaFuncSetAttribute(k_line<T, M, NF, EPI, KIND, R>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         if (e != cudaSuccess) return e;
         attr_done = 1;
     }
     const int nlines = D.nlines(dir);
+    int grid = (nlines + LPB - 1) / LPB;
+    k_line<T, M, NF, EPI, KIND, R><<<grid, threads, sm, st>>>(D, dir, nlines, LPB, tab.view<T>(), op,
+                                                              f, xi, nU, accumulate);
+    return cudaGetLastError();
+}
+
+template <typename T, typename M, int NF, int EPI, int KIND>
+static cudaError_t line_dispatch(const Dims& D, int dir, const HostLineTab& tab, const LineOp& op,
+                                 const Fields<T>& f, const M* xi, int nU, int accumulate,
+                                 cudaStream_t st)
+{
+    const int nlines = D.nlines(dir);
     int LPB, threads;
     size_t sm;
     line_launch_shape(dir, D.n[dir], nlines, NF, sizeof(T), LPB, threads, sm);
     if (sm > 200 * 1024) return cudaErrorInvalidConfiguration;
-    int grid = (nlines + LPB - 1) / LPB;
-    k_line<T, M, NF, EPI, KIND><<<grid, threads, sm, st>>>(D, dir, nlines, LPB, tab.view<T>(), op, f,
-                                                           xi, nU, accumulate);
-    return cudaGetLastError();
+    const int R = slots_per_thread(LPB * D.n[dir], threads);
+    if (R <= 1) return line_dispatch_r<T, M, NF, EPI, KIND, 1>(D, dir, tab, op, f, xi, nU, accumulate, st, LPB, threads, sm);
+    if (R <= 2) return line_dispatch_r<T, M, NF, EPI, KIND, 2>(D, dir, tab, op, f, xi, nU, accumulate, st, LPB, threads, sm);
+    if (R <= 4) return line_dispatch_r<T, M, NF, EPI, KIND, 4>(D, dir, tab, op, f, xi, nU, accumulate, st, LPB, threads, sm);
+    return cudaErrorInvalidConfiguration;
 }
 
 template <typename T, typename M>

@@ -149,12 +149,30 @@ wd_status build_line_table(int N, int periodic, const std::vector<double>& a0v,
     int L = 0;
     while ((1 << L) < N) L++;
     tab.L = implicit ? L : 0;
-    std::vector<double> h((size_t)(2 * L + 2) * N, 0.0);
+    std::vector<double> h((size_t)(2 * L + 3) * N, 0.0);
     double* alpha = h.data();
     double* gamma = alpha + (size_t)L * N;
     double* ib = gamma + (size_t)L * N;
-    double* zt = ib + N;
+    double* ib32 = ib + N;
+    double* zt = ib32 + N;
+    // Early stop: once every row's remaining off-diagonal weight (|a| + |c|) / |b| is below
+    // the rounding of the working precision, further levels change nothing representable;
+    // C6 (alpha = 1/3) gets there in about 6 (float) / 7 (double) levels, the filter with
+    // alpha_f -> 1/2 needs nearly all log2 N levels.
+    auto coupling = [&](void) {
+        double w = 0.0;
+        for (int i = 0; i < N; i++) w = std::max(w, (std::fabs(a[i]) + std::fabs(c[i])) / std::fabs(b[i]));
+        return w;
+    };
+    tab.L64 = tab.L;
+    tab.L32 = tab.L;
+    bool have32 = false;
     if (implicit) {
+        if (coupling() < 1e-9) {
+            tab.L32 = 0;
+            have32 = true;
+            for (int i = 0; i < N; i++) ib32[i] = 1.0 / b[i];
+        }
         for (int lev = 0; lev < L; lev++) {
             int hh = 1 << lev;
             std::vector<double> na(N, 0.0), nb = b, nc(N, 0.0);
@@ -176,10 +194,21 @@ wd_status build_line_table(int N, int periodic, const std::vector<double>& a0v,
             a = na;
             b = nb;
             c = nc;
+            const double w = coupling();
+            if (!have32 && w < 1e-9) {
+                tab.L32 = lev + 1;
+                have32 = true;
+                for (int i = 0; i < N; i++) ib32[i] = 1.0 / b[i];
+            }
+            if (w < 1e-18) {
+                tab.L64 = lev + 1;
+                break;
+            }
         }
     }
     for (int i = 0; i < N; i++) {
         ib[i] = implicit ? 1.0 / b[i] : 1.0;
+        if (!have32) ib32[i] = ib[i];
         zt[i] = z[i];
     }
     size_t nd = h.size();
@@ -222,8 +251,9 @@ static LineTab<T> make_view(const HostLineTab& h, const T* base)
     t.periodic = h.periodic && h.implicit;
     t.alpha = base;
     t.gamma = base + (size_t)L * N;
-    t.ib = base + (size_t)2 * L * N;
-    t.z = base + (size_t)(2 * L + 1) * N;
+    t.ib = base + (size_t)2 * L * N + (sizeof(T) == 4 ? N : 0);
+    t.z = base + (size_t)(2 * L + 2) * N;
+    t.L = sizeof(T) == 4 ? h.L32 : h.L64;
     t.a0 = T(h.a0);
     t.inv_den = T(h.inv_den);
     return t;

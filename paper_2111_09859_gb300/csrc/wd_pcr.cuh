@@ -44,44 +44,94 @@ __device__ __forceinline__ LineMap make_map(const Dims& D, int dir, int LPB, int
     return m;
 }
 
-// value of row i + o of the same line (periodic wrap, optional even reflection; for other
-// non-periodic offsets the caller guarantees 0 <= i + o < N)
-template <typename T>
-__device__ __forceinline__ T nb(const T* F, const LineMap& mp, int l, int i, int o, int per, int reflect)
+// One grid-line node held by a thread: its slot s, node index i on the line, the slot of
+// node 0 of the same line (nodes of a line sit at base + j * si in shared memory), and its
+// global element index.
+struct Slot {
+    int s, i, base;
+    long long node;
+};
+
+// Slots of this thread: s = threadIdx.x + r * blockDim.x, r < R (inactive: s = -1).
+template <int R>
+__device__ __forceinline__ void slots_init(Slot (&q)[R], const LineMap& mp, const Dims& D)
 {
-    int j = i + o;
-    const int N = mp.N;
-    if (per) j = j < 0 ? j + N : (j >= N ? j - N : j);
-    else if (reflect) j = j < 0 ? -j : (j >= N ? 2 * (N - 1) - j : j);
-    return F[mp.slot(l, j)];
+    const long long st = D.stride(mp.dir);
+    const int si = mp.dir == 0 ? 1 : mp.LPB;
+#pragma unroll
+    for (int r = 0; r < R; r++) {
+        const int s = threadIdx.x + r * blockDim.x;
+        q[r].s = -1;
+        q[r].i = 0;
+        q[r].base = 0;
+        q[r].node = 0;
+        if (s < mp.size()) {
+            int l, i;
+            mp.decode(s, l, i);
+            if (l < mp.nl) {
+                q[r].s = s;
+                q[r].i = i;
+                q[r].base = s - i * si;
+                q[r].node = D.line_base(mp.dir, mp.q0 + l) + (long long)i * st;
+            }
+        }
+    }
+}
+
+// read-only view of one line in shared memory: node j at F[base + j * si]
+template <typename T>
+struct LineView {
+    const T* F;
+    int base, si, N, per;
+    __device__ __forceinline__ T at(int j) const   // 0 <= j < N, or wrapped when periodic
+    {
+        if (per) j = j < 0 ? j + N : (j >= N ? j - N : j);
+        return F[base + j * si];
+    }
+    __device__ __forceinline__ T refl(int j) const  // even reflection at non-periodic ends
+    {
+        if (per) j = j < 0 ? j + N : (j >= N ? j - N : j);
+        else j = j < 0 ? -j : (j >= N ? 2 * (N - 1) - j : j);
+        return F[base + j * si];
+    }
+};
+
+template <typename T>
+__device__ __forceinline__ LineView<T> view_of(const T* F, const Slot& q, const LineMap& mp, int per)
+{
+    LineView<T> v;
+    v.F = F;
+    v.base = q.base;
+    v.si = mp.dir == 0 ? 1 : mp.LPB;
+    v.N = mp.N;
+    v.per = per;
+    return v;
 }
 
 // first derivative row at node i (explicit value, or the right-hand side of a compact row);
 // Sec. 3.2.2, Eq. 16.  Non-periodic ends: one-sided (-25,48,-36,16,-3)/12 at the end node,
 // centred (f_2 - f_0)/2 at the next node; E6 uses E4 at the third node.
 template <typename T>
-__device__ __forceinline__ T deriv_rhs(const T* F, const LineMap& mp, int l, int i, int per, int sch)
+__device__ __forceinline__ T deriv_rhs(const LineView<T>& v, int i, int sch)
 {
-    const int N = mp.N;
-#define FV(o) nb(F, mp, l, i, (o), per, 0)
-    if (!per) {
+    const int N = v.N;
+    if (!v.per) {
         if (i == 0)
-            return (T(-25.0) * FV(0) + T(48.0) * FV(1) - T(36.0) * FV(2) + T(16.0) * FV(3)
-                    - T(3.0) * FV(4)) * T(1.0 / 12.0);
+            return (T(-25.0) * v.at(0) + T(48.0) * v.at(1) - T(36.0) * v.at(2) + T(16.0) * v.at(3)
+                    - T(3.0) * v.at(4)) * T(1.0 / 12.0);
         if (i == N - 1)
-            return -(T(-25.0) * FV(0) + T(48.0) * FV(-1) - T(36.0) * FV(-2) + T(16.0) * FV(-3)
-                     - T(3.0) * FV(-4)) * T(1.0 / 12.0);
-        if (i == 1 || i == N - 2) return T(0.5) * (FV(1) - FV(-1));
+            return -(T(-25.0) * v.at(N - 1) + T(48.0) * v.at(N - 2) - T(36.0) * v.at(N - 3)
+                     + T(16.0) * v.at(N - 4) - T(3.0) * v.at(N - 5)) * T(1.0 / 12.0);
+        if (i == 1 || i == N - 2) return T(0.5) * (v.at(i + 1) - v.at(i - 1));
     }
-    T d1 = FV(1) - FV(-1);
+    const T d1 = v.at(i + 1) - v.at(i - 1);
     if (sch == WD_E2) return T(0.5) * d1;
     if (sch == WD_C4) return T(0.75) * d1;
-    T d2 = FV(2) - FV(-2);
+    const T d2 = v.at(i + 2) - v.at(i - 2);
     if (sch == WD_C6) return T(7.0 / 9.0) * d1 + T(1.0 / 36.0) * d2;
-    if (sch == WD_E4 || (!per && (i == 2 || i == N - 3))) return T(2.0 / 3.0) * d1 - T(1.0 / 12.0) * d2;
-    T d3 = FV(3) - FV(-3);
+    if (sch == WD_E4 || (!v.per && (i == 2 || i == N - 3))) return T(2.0 / 3.0) * d1 - T(1.0 / 12.0) * d2;
+    const T d3 = v.at(i + 3) - v.at(i - 3);
     return T(0.75) * d1 - T(0.15) * d2 + T(1.0 / 60.0) * d3;
-#undef FV
 }
 
 // Delta form of the filter of Eq. 21.  With sum_m a_m = 1 + 2 alpha the system
@@ -93,73 +143,87 @@ __device__ __forceinline__ T deriv_rhs(const T* F, const LineMap& mp, int l, int
 // cf[hw][m] holds a_m/2 - alpha [m == 1] of the order-2hw member; the order drops to
 // 2 hw = 2 x (distance to a non-periodic end), and end nodes are not filtered (Sec. 3.4).
 template <typename T>
-__device__ __forceinline__ T filter_rhs(const T* F, const LineMap& mp, int l, int i, int per,
-                                        const T (*cf)[6])
+__device__ __forceinline__ T filter_rhs(const LineView<T>& v, int i, const T (*cf)[6])
 {
     int hw = 5;
-    if (!per) {
-        int e = i < mp.N - 1 - i ? i : mp.N - 1 - i;
+    if (!v.per) {
+        const int e = i < v.N - 1 - i ? i : v.N - 1 - i;
         hw = e < 5 ? e : 5;
     }
     if (hw == 0) return T(0);
-    const T f0 = F[mp.slot(l, i)];
+    const T f0 = v.at(i);
     T s = T(0);
 #pragma unroll
     for (int m = 5; m >= 1; m--)
-        if (m <= hw) s += cf[hw][m] * ((nb(F, mp, l, i, m, per, 0) - f0) + (nb(F, mp, l, i, -m, per, 0) - f0));
+        if (m <= hw) s += cf[hw][m] * ((v.at(i + m) - f0) + (v.at(i - m) - f0));
     return s;
 }
 
 // truncated 9-point Gaussian of Kawai & Lele's LAD, even reflection at non-periodic ends
 template <typename T>
-__device__ __forceinline__ T gauss_rhs(const T* F, const LineMap& mp, int l, int i, int per)
+__device__ __forceinline__ T gauss_rhs(const LineView<T>& v, int i)
 {
-#define GV(o) (nb(F, mp, l, i, (o), per, 1) + nb(F, mp, l, i, -(o), per, 1))
-    return T(3565.0 / 10368.0) * F[mp.slot(l, i)] + T(3091.0 / 12960.0) * GV(1)
-         + T(1997.0 / 25920.0) * GV(2) + T(149.0 / 12960.0) * GV(3) + T(107.0 / 103680.0) * GV(4);
-#undef GV
+    return T(3565.0 / 10368.0) * v.at(i) + T(3091.0 / 12960.0) * (v.refl(i + 1) + v.refl(i - 1))
+         + T(1997.0 / 25920.0) * (v.refl(i + 2) + v.refl(i - 2))
+         + T(149.0 / 12960.0) * (v.refl(i + 3) + v.refl(i - 3))
+         + T(107.0 / 103680.0) * (v.refl(i + 4) + v.refl(i - 4));
 }
 
 // 5-point fourth difference at node i (one-sided near non-periodic ends: the nearest
 // complete stencil), the d^4/dxi^4 of Eq. 7
 template <typename T>
-__device__ __forceinline__ T d4_row(const T* F, const LineMap& mp, int l, int i, int per)
+__device__ __forceinline__ T d4_row(const LineView<T>& v, int i)
 {
     int c = i;
-    if (!per) c = c < 2 ? 2 : (c > mp.N - 3 ? mp.N - 3 : c);
-    return nb(F, mp, l, c, -2, per, 0) - T(4) * nb(F, mp, l, c, -1, per, 0) + T(6) * F[mp.slot(l, c)]
-         - T(4) * nb(F, mp, l, c, 1, per, 0) + nb(F, mp, l, c, 2, per, 0);
+    if (!v.per) c = c < 2 ? 2 : (c > v.N - 3 ? v.N - 3 : c);
+    return v.at(c - 2) - T(4) * v.at(c - 1) + T(6) * v.at(c) - T(4) * v.at(c + 1) + v.at(c + 2);
 }
 
 // Parallel cyclic reduction of NF right-hand sides held in X (field f at X + f*S), with
 // scratch Y of the same size.  Level s combines rows i -/+ 2^s with the precomputed
-// multipliers alpha_s(i), gamma_s(i); after the last level x_i = d_i / b_i.  Periodic
-// lines solve the corner-free matrix B and add the Sherman-Morrison correction
-// x = y - (y_0 - a_0 y_{N-1}) / (1 + z_0 - a_0 z_{N-1}) z with z = B^-1 u precomputed.
-// Returns the buffer holding the solution.  All threads of the block must call it.
-template <typename T, int NF>
-__device__ T* pcr_solve(T* X, T* Y, const LineMap& mp, const LineTab<T>& tb)
+// multipliers alpha_s(i), gamma_s(i) (zero where the neighbour is outside the line; the
+// index is then clamped to the row itself so that no slot outside the line is read); after
+// the last level x_i = d_i / b_i.  The next level's multipliers are loaded before the
+// current level's barrier.  Periodic lines solve the corner-free matrix B and add the
+// Sherman-Morrison correction x = y - (y_0 - a_0 y_{N-1}) / (1 + z_0 - a_0 z_{N-1}) z with
+// z = B^-1 u precomputed.  Returns the buffer holding the solution.  Every thread of the
+// block must call it.
+template <typename T, int NF, int R>
+__device__ T* pcr_solve(T* X, T* Y, const LineMap& mp, const LineTab<T>& tb, const Slot (&q)[R])
 {
     const int S = mp.size(), N = mp.N;
-    const int tid = threadIdx.x, nth = blockDim.x;
+    const int si = mp.dir == 0 ? 1 : mp.LPB;
+    T an[R], gn[R], ib[R];
+#pragma unroll
+    for (int r = 0; r < R; r++) {
+        an[r] = gn[r] = T(0);
+        ib[r] = T(1);
+        if (q[r].s >= 0) {
+            ib[r] = tb.ib[q[r].i];
+            if (tb.L > 0) {
+                an[r] = tb.alpha[q[r].i];
+                gn[r] = tb.gamma[q[r].i];
+            }
+        }
+    }
     for (int lev = 0; lev < tb.L; lev++) {
-        const int h = 1 << lev;
-        const T* al = tb.alpha + (size_t)lev * N;
-        const T* ga = tb.gamma + (size_t)lev * N;
-        for (int s = tid; s < S; s += nth) {
-            int l, i;
-            mp.decode(s, l, i);
-            if (l >= mp.nl) continue;
-            const T a = al[i], g = ga[i];
-            const int sm = i - h >= 0 ? mp.slot(l, i - h) : s;
-            const int sp = i + h < N ? mp.slot(l, i + h) : s;
+        const int h = 1 << lev, hs = h * si;
+#pragma unroll
+        for (int r = 0; r < R; r++) {
+            const int s = q[r].s;
+            const T ac = an[r], gc = gn[r];
+            if (s >= 0 && lev + 1 < tb.L) {
+                an[r] = tb.alpha[(size_t)(lev + 1) * N + q[r].i];
+                gn[r] = tb.gamma[(size_t)(lev + 1) * N + q[r].i];
+            }
+            if (s < 0) continue;
+            const int i = q[r].i;
+            const int sm = i - h >= 0 ? s - hs : s;
+            const int sp = i + h < N ? s + hs : s;
 #pragma unroll
             for (int f = 0; f < NF; f++) {
                 const T* xf = X + (size_t)f * S;
-                T v = xf[s];
-                if (i - h >= 0) v += a * xf[sm];
-                if (i + h < N) v += g * xf[sp];
-                Y[(size_t)f * S + s] = v;
+                Y[(size_t)f * S + s] = xf[s] + ac * xf[sm] + gc * xf[sp];
             }
         }
         __syncthreads();
@@ -167,26 +231,25 @@ __device__ T* pcr_solve(T* X, T* Y, const LineMap& mp, const LineTab<T>& tb)
         X = Y;
         Y = t;
     }
-    for (int s = tid; s < S; s += nth) {
-        int l, i;
-        mp.decode(s, l, i);
-        if (l >= mp.nl) continue;
-        const T ib = tb.ib[i];
 #pragma unroll
-        for (int f = 0; f < NF; f++) X[(size_t)f * S + s] *= ib;
+    for (int r = 0; r < R; r++) {
+        const int s = q[r].s;
+        if (s < 0) continue;
+#pragma unroll
+        for (int f = 0; f < NF; f++) X[(size_t)f * S + s] *= ib[r];
     }
     __syncthreads();
     if (tb.periodic) {
-        for (int s = tid; s < S; s += nth) {
-            int l, i;
-            mp.decode(s, l, i);
-            if (l >= mp.nl) continue;
-            const T z = tb.z[i];
-            const int s0 = mp.slot(l, 0), s1 = mp.slot(l, N - 1);
+#pragma unroll
+        for (int r = 0; r < R; r++) {
+            const int s = q[r].s;
+            if (s < 0) continue;
+            const T z = tb.z[q[r].i];
+            const int s0 = q[r].base, s1 = q[r].base + (N - 1) * si;
 #pragma unroll
             for (int f = 0; f < NF; f++) {
                 const T* xf = X + (size_t)f * S;
-                T corr = (xf[s0] - tb.a0 * xf[s1]) * tb.inv_den;
+                const T corr = (xf[s0] - tb.a0 * xf[s1]) * tb.inv_den;
                 Y[(size_t)f * S + s] = xf[s] - corr * z;
             }
         }
@@ -196,18 +259,24 @@ __device__ T* pcr_solve(T* X, T* Y, const LineMap& mp, const LineTab<T>& tb)
     return X;
 }
 
-// threads per block and lines per block for a line pass with NF fields of type T
+// lines per block and threads per block for a line pass with NF fields of type T: at
+// most 200 KB of shared memory for the two buffers and enough blocks to cover the 152 SMs
+// twice when possible (strided directions prefer several lines per block for coalesced
+// rows); one slot per thread up to 512 slots, otherwise R slots per 512 threads
 inline void line_launch_shape(int dir, int N, int nlines, int nf, size_t esize, int& LPB, int& threads,
                               size_t& smem)
 {
     const size_t limit = 200 * 1024;
-    LPB = dir == 0 ? 1 : 8;
+    LPB = dir == 0 ? 1 : 4;
     auto bytes = [&](int lpb) { return (size_t)2 * nf * lpb * N * esize; };
-    while (LPB > 1 && bytes(LPB) > limit) LPB /= 2;
+    while (LPB > 1 && (bytes(LPB) > limit || LPB * N > 512)) LPB /= 2;
     while (LPB > 1 && (nlines + LPB - 1) / LPB < 2 * 152) LPB /= 2;
-    int slots = LPB * N;
-    threads = slots >= 512 ? 512 : ((slots + 31) / 32) * 32;
+    const int slots = LPB * N;
+    threads = slots > 512 ? 512 : ((slots + 31) / 32) * 32;
     smem = bytes(LPB);
 }
+
+// slots per thread needed by a block of `threads` threads holding `slots` slots
+inline int slots_per_thread(int slots, int threads) { return (slots + threads - 1) / threads; }
 
 }  // namespace wd

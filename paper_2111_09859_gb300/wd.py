@@ -148,7 +148,10 @@ class Grid:
 
         self.shape = tuple(int(s) for s in spec.shape)
         self.ndim = len(self.shape)
+        self.batch = int(getattr(spec, "batch", 1))
         n = list(self.shape) + [1] * (3 - self.ndim)
+        if self.ndim == 2:
+            n[2] = self.batch
         self.n = n
         self.N = n[0] * n[1] * n[2]
         self.precision = precision

@@ -34,6 +34,7 @@ class GridSpec:
     mask: np.ndarray | None = None   # (N,) uint8, 1 = Dirichlet node
     dval: np.ndarray | None = None   # (N,) float64 Dirichlet values
     meta: dict = field(default_factory=dict)
+    batch: int = 1                   # stacked independent 2-D grids (same shape and faces)
 
     @property
     def ndim(self):
@@ -41,7 +42,7 @@ class GridSpec:
 
     @property
     def N(self):
-        return int(np.prod(self.shape))
+        return int(np.prod(self.shape)) * self.batch
 
     def grid_shape(self):
         """numpy array shape (nk, nj, ni) / (nj, ni) of one field."""
@@ -174,3 +175,22 @@ def random_field(spec: GridSpec, seed: int, smooth: bool = True, amp: float = 1.
         ph = rng.uniform(0, 2 * np.pi)
         f += rng.uniform(0.2, 1.0) * np.sin((k[:, None] * spec.xyz).sum(0) + ph)
     return amp * f
+
+
+def stack(specs):
+    """Stack same-shape 2-D grids (same boundary kinds) into one GridSpec with batch =
+    len(specs): grid k occupies nodes k*N .. (k+1)*N - 1 of every array."""
+    first = specs[0]
+    assert len(first.shape) == 2
+    for s in specs:
+        assert s.shape == first.shape and s.bc_lo == first.bc_lo and s.bc_hi == first.bc_hi
+    xyz = np.concatenate([s.xyz for s in specs], axis=1)
+    mask = None
+    if any(s.mask is not None for s in specs):
+        mask = np.concatenate([s.mask if s.mask is not None else np.zeros(s.N, np.uint8) for s in specs])
+    dval = None
+    if any(s.dval is not None for s in specs):
+        dval = np.concatenate([s.dval if s.dval is not None else np.zeros(s.N) for s in specs])
+    return GridSpec(first.name + f"x{len(specs)}", first.shape, xyz, first.bc_lo, first.bc_hi,
+                    period=first.period, L_ref=first.L_ref, mask=mask, dval=dval,
+                    meta=dict(members=[s.meta for s in specs]), batch=len(specs))

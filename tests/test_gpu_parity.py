@@ -243,3 +243,50 @@ def test_pseudo_steps_generic_path(wd, oracle, case, monkeypatch):
     ref, _ = og.hj_steps(phi0, 4, **oracle_kw(scheme, prm))
     out, _ = g.steps(gpu_params(wd, scheme, prm), g.as_field(phi0), 4, kind=0)
     np.testing.assert_allclose(to_np(out), ref, atol=1e-10 * scale(ref), rtol=0)
+
+
+def _cyl_batch(radii, nr=33, nt=64):
+    return [W.cylinder(nr, nt, 1.03 ** (256 / (nr - 1)), r_wall=r) for r in radii]
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_stacked_grids_match_single_grids(wd, oracle, prec):
+    """Stacked 2-D grids (n[2] = batch) run the same launches for every member: K pseudo
+    steps of the stack equal K steps of each grid alone, bit for bit, and the oracle."""
+    import torch
+
+    members = _cyl_batch([0.5, 0.45, 0.55])
+    spec = W.stack(members)
+    prm = base_params(4, equation=1, curvature=1, alpha_f=0.495)
+    gb = wd.Grid(spec, prec, 4)
+    exact = [np.hypot(*m.xyz) - m.meta["r_wall"] for m in members]
+    phi0 = np.concatenate([oracle_grid(oracle, m, 4).apply_bc(e + 0.02 * W.random_field(m, 3))
+                           for m, e in zip(members, exact)])
+    outb, stb = gb.steps(gpu_params(wd, 4, prm), gb.as_field(phi0), 4)
+    outb = to_np(outb)
+    N = members[0].N
+    worst = 0.0
+    for k, m in enumerate(members):
+        g = wd.Grid(m, prec, 4)
+        out, st = g.steps(gpu_params(wd, 4, prm), g.as_field(phi0[k * N:(k + 1) * N]), 4)
+        np.testing.assert_array_equal(outb[k * N:(k + 1) * N], to_np(out))
+        worst = max(worst, st["res_l2"])
+        ref, _ = oracle_grid(oracle, m, 4).hj_steps(phi0[k * N:(k + 1) * N], 4, **oracle_kw(4, prm))
+        tol = 1e-10 if prec == 0 else 1e-5
+        np.testing.assert_allclose(outb[k * N:(k + 1) * N], ref, atol=tol * scale(ref), rtol=0)
+    assert stb["res_l2"] == pytest.approx(worst, rel=1e-12)
+
+
+def test_stacked_solve_against_oracle(wd, oracle):
+    members = _cyl_batch([0.5, 0.4])
+    spec = W.stack(members)
+    prm = base_params(4, equation=1, curvature=1, alpha_f=0.495, tol_l2=1e-7)
+    gb = wd.Grid(spec, wd.FP32_METRIC64, 4)
+    out, st = gb.solve(gpu_params(wd, 4, prm))
+    assert st["converged"], st
+    out = to_np(out)
+    N = members[0].N
+    for k, m in enumerate(members):
+        ref, ost = oracle_grid(oracle, m, 4).solve(**oracle_kw(4, dict(prm, tol_l2=1e-12)))
+        assert ost["converged"]
+        assert np.abs(out[k * N:(k + 1) * N] - ref).max() <= 2e-4
