@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "wd_api_internal.h"
+#include "wd_cart3d.h"
 #include "wd_fused2d.h"
 
 using namespace wd;
@@ -81,6 +82,8 @@ struct wd_grid_s {
     int nred = 0;
     int npartial = 0;           // capacity of `partial` in blocks
     int force_generic = 0;      // WD_FORCE_GENERIC=1 at creation: never use the fused path
+    int cart = 0;               // uniform Cartesian 3-D grid (diagonal constant metrics)
+    double h[3] = {0, 0, 0};    // its spacings
     HostLineTab dtab[3], ftab[3], etab[3];
     // kernel timer (wd_profile)
     int prof_on = 0;
@@ -552,11 +555,80 @@ struct Solver {
         return WD_OK;
     }
 
+    // uniform Cartesian 3-D grids with an explicit scheme and walls / periodic faces only
+    bool cart3d() const
+    {
+        if (D.ndim != 3 || !g->cart || g->force_generic) return false;
+        const int sch = g->desc.scheme;
+        if (sch == WD_C4 || sch == WD_C6) return false;
+        for (int d = 0; d < 3; d++)
+            for (int k : {g->desc.bc_lo[d], g->desc.bc_hi[d]})
+                if (k == WD_BC_FARFIELD || k == WD_BC_NEUMANN) return false;
+        return true;
+    }
+
+    wd_status step_cart3d(bool poisson)
+    {
+        if (p->filter) ST(ensure_filter(p->alpha_f));
+        C3Args<T> a;
+        std::memset(&a, 0, sizeof(a));
+        a.D = D;
+        a.scheme = g->desc.scheme;
+        for (int l = 0; l < 3; l++) {
+            a.ih[l] = 1.0 / g->h[l];
+            a.slad[l] = std::pow(g->h[l], p->lad_exp - 4.0);
+            a.sig1 += 1.0 / g->h[l];
+            a.sig2 += 1.0 / (g->h[l] * g->h[l]);
+        }
+        a.phin = W(W_PHIN);
+        a.acc = W(W_ACC);
+        a.dtv = W(W_DT);
+        a.U0 = W(W_U0);
+        a.U1 = W(W_U1);
+        a.U2 = W(W_U2);
+        a.L = W(W_N0);
+        a.G1 = W(W_N1);
+        a.G2 = W(W_N2);
+        a.mask = g->mask;
+        a.dval = (const T*)g->dval;
+        a.eps = p->eps;
+        a.cfl = p->cfl;
+        a.C_lad = p->C_lad;
+        a.equation = p->equation;
+        a.lad = p->equation == WD_HJ_LAD && !poisson;
+        a.poisson = poisson;
+        for (int s = 0; s < 4; s++) {
+            a.src = s == 0 ? W(W_PHIN) : W(W_PHIS);
+            a.dst = W(W_PHIS);
+            a.stage = s;
+            {
+                ProfScope ps(g, WD_K_DERIV);
+                CK(c3_launch<T>(a, C3_U, st));
+            }
+            if (a.lad) {
+                ProfScope ps(g, WD_K_GAUSS);
+                CK(c3_launch<T>(a, C3_GX, st));
+                CK(c3_launch<T>(a, C3_GY, st));
+            }
+            ProfScope ps(g, WD_K_POINT);
+            CK(c3_launch<T>(a, C3_S, st));
+        }
+        if (p->filter) {
+            for (int d = 0; d < 3; d++) ST(filter_dir(d, p->alpha_f, W(W_PHIS), W(W_PHIS)));
+            ST(bc(W(W_PHIS), poisson));
+        }
+        ProfScope ps(g, WD_K_NORM);
+        CK(launch_norms<T>(D, W(W_PHIS), W(W_PHIN), g->mask, g->partial, g->counter, g->result,
+                           g->nred, st));
+        return WD_OK;
+    }
+
     // one pseudo step from W_PHIN; leaves the new state in W_PHIN and the change norms in
     // g->result
     wd_status step(bool poisson)
     {
         if (fused2d()) return step_fused(poisson);
+        if (cart3d() && !(p->curvature && !poisson)) return step_cart3d(poisson);
         if (g->batch > 1) return set_error(WD_ERR_INVALID_ARG, "stacked 2-D grids need the fused path");
         for (int s = 0; s < 4; s++) {
             const T* src = s == 0 ? W(W_PHIN) : W(W_PHIS);
@@ -792,6 +864,31 @@ static wd_status create_impl(wd_grid g, const double* xyz_host, const uint8_t* m
         CK(cudaMemcpy2DAsync(g->xyz + m * tot, (size_t)D.pitch * 8,
                              xyz_host + (size_t)m * D.n[0] * D.n[1] * D.n[2], (size_t)D.n[0] * 8,
                              (size_t)D.n[0] * 8, (size_t)D.n[1] * D.n[2], cudaMemcpyHostToDevice, st));
+    // uniform Cartesian 3-D grid?  x = x0 + i hx, y = y0 + j hy, z = z0 + k hz at every node
+    if (D.ndim == 3) {
+        const size_t N = (size_t)D.n[0] * D.n[1] * D.n[2];
+        const double* X = xyz_host;
+        const double *Y = xyz_host + N, *Z = xyz_host + 2 * N;
+        const size_t s1 = D.n[0], s2 = (size_t)D.n[0] * D.n[1];
+        double hx = X[1] - X[0], hy = Y[s1] - Y[0], hz = Z[s2] - Z[0];
+        bool ok = hx > 0 && hy > 0 && hz > 0;
+        const double tx = 1e-9 * (std::fabs(X[0]) + D.n[0] * hx), ty = 1e-9 * (std::fabs(Y[0]) + D.n[1] * hy),
+                     tz = 1e-9 * (std::fabs(Z[0]) + D.n[2] * hz);
+        for (int k = 0; k < D.n[2] && ok; k++)
+            for (int j = 0; j < D.n[1] && ok; j++)
+                for (int i = 0; i < D.n[0]; i++) {
+                    const size_t q = i + s1 * j + s2 * k;
+                    if (std::fabs(X[q] - (X[0] + i * hx)) > tx || std::fabs(Y[q] - (Y[0] + j * hy)) > ty ||
+                        std::fabs(Z[q] - (Z[0] + k * hz)) > tz) {
+                        ok = false;
+                        break;
+                    }
+                }
+        g->cart = ok;
+        g->h[0] = hx;
+        g->h[1] = hy;
+        g->h[2] = hz;
+    }
     // line tables
     for (int d = 0; d < D.ndim; d++) {
         std::vector<double> a, c;

@@ -290,3 +290,23 @@ def test_stacked_solve_against_oracle(wd, oracle):
         ref, ost = oracle_grid(oracle, m, 4).solve(**oracle_kw(4, dict(prm, tol_l2=1e-12)))
         assert ost["converged"]
         assert np.abs(out[k * N:(k + 1) * N] - ref).max() <= 2e-4
+
+
+@pytest.mark.parametrize("scheme,eq", [(2, 1), (1, 0), (0, 2)])
+@pytest.mark.parametrize("generic", [False, True])
+def test_duct_steps_both_paths(wd, oracle, scheme, eq, generic, monkeypatch):
+    """Uniform Cartesian 3-D grids take the stencil path (wd_cart3d.cu) unless
+    WD_FORCE_GENERIC=1; both agree with the oracle over 4 pseudo steps (and Poisson steps)."""
+    if generic:
+        monkeypatch.setenv("WD_FORCE_GENERIC", "1")
+    spec = W.duct(14, nx=10)
+    prm = base_params(scheme, equation=eq)
+    og = oracle_grid(oracle, spec, scheme)
+    g = wd.Grid(spec, 0, scheme)
+    phi0 = og.apply_bc(exact_of(spec) + 0.02 * W.random_field(spec, 21))
+    ref, _ = og.hj_steps(phi0, 4, **oracle_kw(scheme, prm))
+    out, _ = g.steps(gpu_params(wd, scheme, prm), g.as_field(phi0), 4, kind=0)
+    np.testing.assert_allclose(to_np(out), ref, atol=1e-10 * scale(ref), rtol=0)
+    refp, _ = og.poisson_steps(np.zeros(spec.N), 10, **oracle_kw(scheme, prm))
+    outp, _ = g.steps(gpu_params(wd, scheme, prm), g.as_field(np.zeros(spec.N)), 10, kind=1)
+    np.testing.assert_allclose(to_np(outp), refp, atol=1e-10 * scale(refp), rtol=0)
