@@ -660,13 +660,18 @@ static double metric_sum1(const or_ctx* C, int p)   /* sum_l |grad xi_l| */
     return s;
 }
 
-static double metric_sum2(const or_ctx* C, int p)   /* sum_l |grad xi_l|^2 */
+/* sum_l sum_k |grad xi_l . grad xi_k|: the Gershgorin bound of the metric tensor of the
+ * second-order term (equal to sum_l |grad xi_l|^2 on orthogonal grids); the local pseudo
+ * time step uses it so that the cross terms of skewed grids are covered */
+static double metric_sum2(const or_ctx* C, int p)
 {
     double s = 0.0;
     for (int l = 0; l < C->g.ndim; l++)
-        for (int m = 0; m < C->g.ndim; m++) {
-            double x = C->xi[(l * 3 + m) * C->N + p];
-            s += x * x;
+        for (int k = 0; k < C->g.ndim; k++) {
+            double q = 0.0;
+            for (int m = 0; m < C->g.ndim; m++)
+                q += C->xi[(l * 3 + m) * C->N + p] * C->xi[(k * 3 + m) * C->N + p];
+            s += fabs(q);
         }
     return s;
 }

@@ -588,11 +588,16 @@ __global__ void k_metric_finish(Dims D, const double* __restrict__ A, double* xi
                 if (m < nd && l < nd) col += a[m][l] * a[m][l];
             }
             dx[(long long)l * tot + e] = l < nd ? sqrt(col) : 0.0;
-            if (l < nd) {
-                s1 += sqrt(q);
-                s2 += q;
-            }
+            if (l < nd) s1 += sqrt(q);
         }
+        // time-step bound of the second-order term: Gershgorin sum of the contravariant
+        // metric tensor g^{lk} = grad(xi_l) . grad(xi_k), cross terms included
+        for (int l = 0; l < nd; l++)
+            for (int k = 0; k < nd; k++) {
+                double q = 0.0;
+                for (int m = 0; m < nd; m++) q += inv[l][m] * inv[k][m];
+                s2 += fabs(q);
+            }
         sig1[e] = M(s1);
         sig2[e] = M(s2);
     }

@@ -163,3 +163,31 @@ def test_lad_constant_sensitivity(oracle):
         phi, _ = g.solve(equation=1, C_lad=C, tol_l2=1e-12, poisson_max_iters=100, poisson_tol=0)
         e.append(np.sqrt(((phi - ex) ** 2).mean()))
     assert abs(e[1] - e[0]) / e[0] < 0.15
+
+
+def sampled_ellipse_distance(sp, n=16384):
+    """Distance from every node to the nearest of n points sampled uniformly in the
+    parameter on the ellipse (sampling error below half the largest chord)."""
+    a, b = sp.meta["a"], sp.meta["b"]
+    t = 2 * np.pi * np.arange(n) / n
+    wx, wy = a * np.cos(t), b * np.sin(t)
+    x, y = sp.xyz
+    d = np.full(x.shape, np.inf)
+    for k in range(0, n, 2048):
+        d = np.minimum(d, np.hypot(x[:, None] - wx[None, k:k + 2048], y[:, None] - wy[None, k:k + 2048]).min(1))
+    return d
+
+
+@pytest.mark.parametrize("aspect", [1.16, 3.46])
+def test_ellipse_against_sampled_distance(oracle, aspect):
+    """Ellipse O-grids (axis ratio up to 3.46, skewed cells near the tips) converge and
+    match the brute-force distance to 16384 sampled wall points within the 65x128
+    discretisation error."""
+    sp = W.ellipse(65, 128, aspect)
+    g = grid_of(oracle, sp, 4)
+    phi, st = g.solve(equation=1, scheme=4, cfl=0.6, tol_l2=1e-6, max_iters=2000,
+                      poisson_max_iters=100, alpha_f=0.49)
+    assert st["converged"] and not st["diverged"]
+    err = np.abs(phi - sampled_ellipse_distance(sp))
+    assert err.max() <= 1.5e-2
+    assert np.sqrt((err ** 2).mean()) <= 5e-3
