@@ -57,9 +57,12 @@ enum { WD_BC_WALL = 0,      /* Dirichlet phi = 0 on the face (Eq. 22) */
 
 /* state / metric precision */
 enum { WD_FP64 = 0,          /* everything double */
-       WD_FP32_METRIC64 = 1, /* float state, stencils and line solves; metrics stored and
-                                applied (chain rule, divergence) in double */
-       WD_FP32 = 2 };        /* float state and metrics (metrics still computed in double) */
+       WD_FP32_METRIC64 = 1, /* float state, stencils, LAD and line solves; the metric
+                                Jacobians (coordinate derivatives and their inverse) are
+                                computed in double at creation and rounded to float for the
+                                loop; change norms accumulate in double */
+       WD_FP32 = 2 };        /* as WD_FP32_METRIC64, but the coordinates are rounded to float
+                                and differentiated in float before the (double) inversion */
 
 /* equation (Sec. 2.3) */
 enum { WD_HJ_STD = 0,        /* Gamma = eps * phi (Eq. 6) */
@@ -243,6 +246,78 @@ wd_status wd_profile_read(wd_grid g, int cls, double* ms_total, long long* launc
 wd_status wd_change_norms_noalloc(const void* new_dev, const void* old_dev,
                                   const uint8_t* mask_dev, long long n, int precision,
                                   double scale, double* norms_dev, void* cuda_stream);
+
+/* ---- geometry reuse ---------------------------------------------------------------- */
+
+/* Replaces the coordinates and the caller Dirichlet set of an existing grid without any
+ * device allocation: same descriptor, new xyz_host / mask_host / dval_host (as for
+ * wd_create_grid).  Recomputes the metrics (Sec. 3.1), the LAD scales and the far-field
+ * spacing ratios on the grid's stream.  Temporary device memory comes from the CUDA
+ * stream-ordered allocator, so the call never waits for work on other streams.
+ * Errors: WD_ERR_INVALID_ARG for a NULL grid or xyz_host; WD_ERR_OOM; WD_ERR_CUDA. */
+wd_status wd_reset_geometry(wd_grid g, const double* xyz_host, const uint8_t* mask_host,
+                            const double* dval_host);
+
+/* ---- request loop (continuous batching of independent solves) ---------------------- */
+
+/* A server owns one scheduler thread on the current device.  Submitted requests wait in
+ * a FIFO queue and are admitted while the sum of the device footprints of the admitted
+ * requests (wd_query_footprint) stays within max_device_bytes and at most max_active run
+ * at once.  Every admitted request runs the solve of wd_solve as a resumable task on its
+ * grid's own stream, one slice of check_every pseudo steps (a CUDA graph) at a time, so
+ * the slices of all admitted requests overlap on the GPU; a request that arrives while
+ * others run is admitted as soon as memory and a slot are free, and finished requests
+ * free theirs at once.  Each request gives the same result as wd_solve alone (the same
+ * kernels, the same slicing and the same convergence checks).  Grids the server creates
+ * are kept per shape for reuse (wd_reset_geometry), within the same memory cap. */
+typedef struct wd_server_s* wd_server;
+
+typedef struct {
+    size_t max_device_bytes;   /* admission cap; 0 = 80% of the free device memory at creation */
+    int max_active;            /* requests running at once; 0 = 32 */
+    int pool_per_shape;        /* idle grids kept per shape; 0 = 2, < 0 = none */
+} wd_server_config;
+
+/* Errors: WD_ERR_INVALID_ARG for NULL out or negative limits; WD_ERR_CUDA. */
+wd_status wd_server_create(const wd_server_config* cfg, wd_server* out);
+
+/* New request on a grid the server creates from desc, xyz_host, mask_host, dval_host (the
+ * arguments of wd_create_grid; copied before the call returns).  phi receives the
+ * wall distance: n[0]*n[1]*n[2] values of the grid's state precision, in device memory or
+ * page-locked host memory, owned by the caller and left untouched until the request is
+ * done; with p->init == WD_INIT_GIVEN it also holds the initial state.  *ticket
+ * identifies the request.
+ * Errors: WD_ERR_INVALID_ARG (bad descriptor or parameters, NULL pointers);
+ * WD_ERR_OOM when the request alone is larger than max_device_bytes. */
+wd_status wd_server_submit(wd_server s, const wd_grid_desc* desc, const double* xyz_host,
+                           const uint8_t* mask_host, const double* dval_host,
+                           const wd_solve_params* p, void* phi, long long* ticket);
+
+/* New request on a grid the caller owns (a session that keeps its state on the device
+ * across requests, e.g. the receding-surface re-solves of wd_step_unsteady).  mask_dev /
+ * dval_dev (or NULL) update the Dirichlet set first as in wd_step_unsteady; warm != 0
+ * starts from phi.  The request is ordered after the work queued on the grid's stream
+ * (wd_set_stream) at the time of the call; the grid must not be used by the caller until
+ * the request is done.  Its footprint counts against the cap while it runs. */
+wd_status wd_server_submit_grid(wd_server s, wd_grid g, const uint8_t* mask_dev,
+                                const void* dval_dev, int warm, const wd_solve_params* p,
+                                void* phi, long long* ticket);
+
+/* Waits up to timeout_s seconds (< 0: no limit) for the request.  On completion fills
+ * *stats, *latency_s (submission to completion, host clock) and returns the request's
+ * own status (WD_OK, WD_ERR_NOT_CONVERGED, ...), and the ticket is released.
+ * Returns WD_ERR_TIMEOUT if the request is still queued or running (the ticket stays
+ * valid), WD_ERR_INVALID_ARG for an unknown ticket. */
+wd_status wd_server_wait(wd_server s, long long ticket, double timeout_s, wd_stats* stats,
+                         double* latency_s);
+
+/* Counters since creation: requests queued, running, done; device bytes admitted now;
+ * peak number of requests running at once. */
+wd_status wd_server_info(wd_server s, long long* queued, long long* running, long long* done,
+                         size_t* admitted_bytes, long long* peak_running);
+
+/* Finishes every submitted request, stops the thread and frees every server-owned grid. */
+void wd_server_destroy(wd_server s);
 
 #ifdef __cplusplus
 }

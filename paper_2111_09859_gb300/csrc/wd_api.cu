@@ -85,6 +85,13 @@ struct wd_grid_s {
     int cart = 0;               // uniform Cartesian 3-D grid (diagonal constant metrics)
     double h[3] = {0, 0, 0};    // its spacings
     HostLineTab dtab[3], ftab[3], etab[3];
+    // CUDA graphs of n pseudo steps, one per kind (HJ, Poisson), reused while the launch
+    // arguments they captured are unchanged: same n, same parameters, same table generation
+    unsigned gen = 0;                    // bumped when tables, scales or geometry change
+    cudaGraphExec_t gx[2] = {nullptr, nullptr};
+    int gx_n[2] = {0, 0};
+    unsigned gx_gen[2] = {0, 0};
+    wd_solve_params gx_p[2];
     // kernel timer (wd_profile)
     int prof_on = 0;
     std::vector<cudaEvent_t> ev_pool;
@@ -136,7 +143,10 @@ struct ProfScope {
     }
 };
 
-static bool metric_double(int prec) { return prec != WD_FP32; }
+// metric type of the pseudo-step loop: FP64 only for the FP64 state.  FP32_METRIC64 computes
+// the metric Jacobians in FP64 (create time) and runs the loop in FP32 on their rounded
+// values; FP32 also takes the coordinate derivatives of the metrics in FP32
+static bool metric_double(int prec) { return prec == WD_FP64; }
 
 // Every call runs on the grid's own stream (graph capture needs a non-legacy stream), ordered
 // after the work already queued on the caller's stream; on exit the caller's stream waits
@@ -261,6 +271,8 @@ static void release(wd_grid g)
         free_line_table(g->etab[k]);
     }
     for (auto& e : g->ev_pool) cudaEventDestroy(e);
+    for (int k = 0; k < 2; k++)
+        if (g->gx[k]) cudaGraphExecDestroy(g->gx[k]);
     if (g->ev_in) cudaEventDestroy(g->ev_in);
     if (g->ev_out) cudaEventDestroy(g->ev_out);
     if (g->stream) cudaStreamDestroy(g->stream);
@@ -292,6 +304,7 @@ struct Solver {
             filter_rows(al, D.n[d], D.per[d], a, c, imp);
             ST(build_line_table(D.n[d], D.per[d], a, c, imp, t));
             t.key = al;
+            g->gen++;
         }
         return WD_OK;
     }
@@ -300,6 +313,7 @@ struct Solver {
         if (g->lads_exp == ex) return WD_OK;
         CK(launch_lad_scale<M>(D, g->xi_d, g->dx_d, ex, (M*)g->lads, st));
         g->lads_exp = ex;
+        g->gen++;
         return WD_OK;
     }
 
@@ -647,14 +661,9 @@ struct Solver {
 
     // Runs n pseudo steps.  Without the kernel timer the steps are captured once into a
     // CUDA graph (n steps per graph) and replayed, so the launch sequence costs one graph
-    // launch per n steps; the first step of a call always runs uncaptured so that every
-    // table and kernel attribute exists before capture.
-    cudaGraphExec_t gexec = nullptr;
-    int gexec_n = 0, gexec_poisson = -1;
-    ~Solver()
-    {
-        if (gexec) cudaGraphExecDestroy(gexec);
-    }
+    // launch per n steps.  The graph stays with the grid and is reused by later solves with
+    // the same n and parameters; the first step of a solve phase runs uncaptured so that
+    // every table and kernel attribute exists before a capture.
     wd_status run_steps(bool poisson, int n, bool& warmed)
     {
         if (n <= 0) return WD_OK;
@@ -663,9 +672,12 @@ struct Solver {
             warmed = true;
             return WD_OK;
         }
-        if (!gexec || gexec_n != n || gexec_poisson != (int)poisson) {
-            if (gexec) cudaGraphExecDestroy(gexec);
-            gexec = nullptr;
+        const int k = poisson ? 1 : 0;
+        const bool hit = g->gx[k] && g->gx_n[k] == n && g->gx_gen[k] == g->gen &&
+                         std::memcmp(&g->gx_p[k], p, sizeof(*p)) == 0;
+        if (!hit) {
+            if (g->gx[k]) cudaGraphExecDestroy(g->gx[k]);
+            g->gx[k] = nullptr;
             cudaGraph_t graph = nullptr;
             CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
             wd_status rs = WD_OK;
@@ -676,24 +688,29 @@ struct Solver {
                 return rs;
             }
             CK(ce);
-            ce = cudaGraphInstantiate(&gexec, graph, 0);
+            cudaGraphExec_t ex = nullptr;
+            ce = cudaGraphInstantiate(&ex, graph, 0);
             cudaGraphDestroy(graph);
             CK(ce);
-            gexec_n = n;
-            gexec_poisson = poisson;
+            g->gx[k] = ex;
+            g->gx_n[k] = n;
+            g->gx_gen[k] = g->gen;
+            g->gx_p[k] = *p;
         }
-        CK(cudaGraphLaunch(gexec, st));
+        CK(cudaGraphLaunch(g->gx[k], st));
         return WD_OK;
     }
 
     // change norms of the last pseudo step; stacked grids report their worst member
-    wd_status read_norms(double scale, double* l2, double* linf)
+    cudaError_t enqueue_norms()
     {
-        const int B = g->batch;
-        CK(cudaMemcpyAsync(g->hres, g->result, (size_t)2 * B * sizeof(double), cudaMemcpyDeviceToHost, st));
-        CK(cudaStreamSynchronize(st));
+        return cudaMemcpyAsync(g->hres, g->result, (size_t)2 * g->batch * sizeof(double),
+                               cudaMemcpyDeviceToHost, st);
+    }
+    void eval_norms(double scale, double* l2, double* linf) const
+    {
         double a = 0.0, b = 0.0;
-        for (int k = 0; k < B; k++) {
+        for (int k = 0; k < g->batch; k++) {
             const double n = g->nact[k] > 0 ? (double)g->nact[k] : 1.0;
             const double l = std::sqrt(g->hres[2 * k] / n) / scale;
             const double m = g->hres[2 * k + 1] / scale;
@@ -702,6 +719,12 @@ struct Solver {
         }
         *l2 = a;
         *linf = b;
+    }
+    wd_status read_norms(double scale, double* l2, double* linf)
+    {
+        CK(enqueue_norms());
+        CK(cudaStreamSynchronize(st));
+        eval_norms(scale, l2, linf);
         return WD_OK;
     }
 
@@ -713,90 +736,148 @@ struct Solver {
         return WD_OK;
     }
 
-    // full solve; phi_user is read for WD_INIT_GIVEN (or warm) and receives the result
-    wd_status solve(void* phi_user, wd_stats* stats, bool warm)
-    {
-        const double L = g->desc.L_ref;
-        int every = p->check_every > 0 ? p->check_every : 1;
+    // ---- a solve as a resumable task ------------------------------------------------
+    // begin() enqueues the initial state; each enqueue() queues one slice of pseudo steps
+    // that ends at a convergence check (every check_every steps) together with the copy of
+    // its change norms; complete(), called once that slice has finished on the device,
+    // evaluates the norms and advances the state; finish() queues the copy-out.  solve()
+    // runs the same sequence synchronously, so a solve gives identical results whether it
+    // runs alone or interleaved with others.
+    struct Run {
+        int phase = 0;                 // 0 Poisson guess, 1 HJ marching, 2 finished
+        int it = 0, pit = 0, every = 1;
+        bool warmed = false, check = false, have_tol = false;
+        double l2 = 0.0, li = 0.0, best = INFINITY;
+        int since_best = 0;
         wd_stats s;
-        std::memset(&s, 0, sizeof(s));
-        int init = warm ? WD_INIT_GIVEN : p->init;
+        wd_status rc = WD_OK;
+    } R;
+
+    wd_status enter_hj(bool after_poisson)
+    {
+        if (after_poisson) ST(spalding_from_phin());
+        ST(bc(W(W_PHIN), false));
+        R.phase = p->max_iters > 0 ? 1 : 2;
+        R.warmed = false;
+        return WD_OK;
+    }
+
+    wd_status begin(const void* phi_user, bool warm)
+    {
+        R = Run();
+        std::memset(&R.s, 0, sizeof(R.s));
+        R.every = p->check_every > 0 ? p->check_every : 1;
+        R.have_tol = p->tol_l2 > 0.0 || p->tol_linf > 0.0;
+        const int init = warm ? WD_INIT_GIVEN : p->init;
         if (init == WD_INIT_GIVEN) {
             CK(to_padded(g, W(W_PHIN), phi_user, sizeof(T)));
         } else {
             CK(launch_fill<T>(W(W_PHIN), D.total, T(0), st));
         }
-        bool warmed = false;
-        if (init == WD_INIT_POISSON) {
+        if (init == WD_INIT_POISSON && p->poisson_max_iters > 0) {
             ST(bc(W(W_PHIN), true));
-            int it = 0;
-            double l2 = 0, li = 0;
-            while (it < p->poisson_max_iters) {
-                int n = std::min(every - it % every, p->poisson_max_iters - it);
-                ST(run_steps(true, n, warmed));
-                it += n;
-                if (p->poisson_tol > 0.0 && it % every == 0) {
-                    ST(read_norms(L * L, &l2, &li));
-                    if (!std::isfinite(l2) || !std::isfinite(li)) break;
-                    if (l2 <= p->poisson_tol) break;
-                }
-            }
-            s.poisson_iters = it;
-            ST(spalding_from_phin());
+            R.phase = 0;
+            return WD_OK;
         }
-        ST(bc(W(W_PHIN), false));
-        int it = 0;
-        double l2 = 0, li = 0;
-        bool have_tol = p->tol_l2 > 0.0 || p->tol_linf > 0.0;
-        bool checked_last = true;
-        wd_status rc = WD_OK;
-        const bool float_state = sizeof(T) == 4;
-        const int stall_steps = 200;
-        double best = INFINITY;
-        int since_best = 0;
-        warmed = false;
-        while (it < p->max_iters) {
-            int n = std::min(every - it % every, p->max_iters - it);
-            ST(run_steps(false, n, warmed));
-            it += n;
-            checked_last = false;
-            if (it % every == 0 || it == p->max_iters) {
-                ST(read_norms(L, &l2, &li));
-                checked_last = true;
-                if (!std::isfinite(l2) || !std::isfinite(li)) {
-                    s.diverged = 1;
-                    rc = WD_ERR_DIVERGED;
-                    break;
-                }
-                if (have_tol && (p->tol_l2 <= 0.0 || l2 <= p->tol_l2) &&
-                    (p->tol_linf <= 0.0 || li <= p->tol_linf)) {
-                    s.converged = 1;
-                    break;
-                }
-                if (l2 < 0.95 * best) {
-                    best = l2;
-                    since_best = 0;
-                } else {
-                    since_best += every;
-                }
-                if (float_state && have_tol && since_best >= stall_steps) {
-                    s.converged = 1;
-                    s.stalled = 1;
-                    break;
-                }
-            }
+        return enter_hj(init == WD_INIT_POISSON);
+    }
+
+    bool finished() const { return R.phase >= 2; }
+
+    wd_status enqueue()
+    {
+        if (R.phase == 0) {
+            const int n = std::min(R.every - R.pit % R.every, p->poisson_max_iters - R.pit);
+            ST(run_steps(true, n, R.warmed));
+            R.pit += n;
+            R.check = p->poisson_tol > 0.0 && R.pit % R.every == 0;
+        } else if (R.phase == 1) {
+            const int n = std::min(R.every - R.it % R.every, p->max_iters - R.it);
+            ST(run_steps(false, n, R.warmed));
+            R.it += n;
+            R.check = true;     // every slice ends on a multiple of check_every or at max_iters
+        } else {
+            R.check = false;
         }
-        if (!checked_last) ST(read_norms(L, &l2, &li));
-        if (rc == WD_OK && have_tol && !s.converged) rc = WD_ERR_NOT_CONVERGED;
-        s.iters = it;
-        s.res_l2 = l2;
-        s.res_linf = li;
-        s.device_bytes = g->bytes;
+        if (R.check) CK(enqueue_norms());
+        return WD_OK;
+    }
+
+    wd_status complete()
+    {
+        const double L = g->desc.L_ref;
+        if (R.phase == 0) {
+            bool done = R.pit >= p->poisson_max_iters;
+            if (R.check) {
+                double l2, li;
+                eval_norms(L * L, &l2, &li);
+                if (!std::isfinite(l2) || !std::isfinite(li) || l2 <= p->poisson_tol) done = true;
+            }
+            if (done) {
+                R.s.poisson_iters = R.pit;
+                ST(enter_hj(true));
+            }
+            return WD_OK;
+        }
+        if (R.phase != 1) return WD_OK;
+        eval_norms(L, &R.l2, &R.li);
+        if (!std::isfinite(R.l2) || !std::isfinite(R.li)) {
+            R.s.diverged = 1;
+            R.rc = WD_ERR_DIVERGED;
+            R.phase = 2;
+            return WD_OK;
+        }
+        if (R.have_tol && (p->tol_l2 <= 0.0 || R.l2 <= p->tol_l2) &&
+            (p->tol_linf <= 0.0 || R.li <= p->tol_linf)) {
+            R.s.converged = 1;
+            R.phase = 2;
+            return WD_OK;
+        }
+        if (R.l2 < 0.95 * R.best) {
+            R.best = R.l2;
+            R.since_best = 0;
+        } else {
+            R.since_best += R.every;
+        }
+        // FP32 state: the change norm stops falling at the round-off floor; stop when the
+        // best RMS change has not improved by 5 % over 200 steps
+        if (sizeof(T) == 4 && R.have_tol && R.since_best >= 200) {
+            R.s.converged = 1;
+            R.s.stalled = 1;
+            R.phase = 2;
+            return WD_OK;
+        }
+        if (R.it >= p->max_iters) R.phase = 2;
+        return WD_OK;
+    }
+
+    // queues the copy of the result into phi_user; the stats are final once it has run
+    wd_status finish(void* phi_user, wd_stats* stats)
+    {
+        wd_status rc = R.rc;
+        if (rc == WD_OK && R.have_tol && !R.s.converged) rc = WD_ERR_NOT_CONVERGED;
+        R.s.iters = R.it;
+        R.s.res_l2 = R.l2;
+        R.s.res_linf = R.li;
+        R.s.device_bytes = g->bytes;
         CK(from_padded(g, phi_user, W(W_PHIN), sizeof(T)));
-        CK(cudaStreamSynchronize(st));
-        if (stats) *stats = s;
+        if (stats) *stats = R.s;
         if (rc == WD_ERR_DIVERGED) set_error(rc, "non-finite pseudo-step change");
         if (rc == WD_ERR_NOT_CONVERGED) set_error(rc, "max_iters reached before the tolerance");
+        return rc;
+    }
+
+    // full solve; phi_user is read for WD_INIT_GIVEN (or warm) and receives the result
+    wd_status solve(void* phi_user, wd_stats* stats, bool warm)
+    {
+        ST(begin(phi_user, warm));
+        while (!finished()) {
+            ST(enqueue());
+            if (R.check) CK(cudaStreamSynchronize(st));
+            ST(complete());
+        }
+        wd_status rc = finish(phi_user, stats);
+        CK(cudaStreamSynchronize(st));
         return rc;
     }
 
@@ -841,7 +922,6 @@ static wd_status dispatch(wd_grid g, F&& fn)
         auto r = fn((double*)nullptr, (double*)nullptr);
         return r;
     }
-    case WD_FP32_METRIC64: return fn((float*)nullptr, (double*)nullptr);
     default: return fn((float*)nullptr, (float*)nullptr);
     }
 }
@@ -850,21 +930,104 @@ static wd_status dispatch(wd_grid g, F&& fn)
 // grid creation
 // ------------------------------------------------------------------------------------
 
+// device arrays whose size and contents depend on the descriptor only
 template <typename T, typename M>
-static wd_status create_impl(wd_grid g, const double* xyz_host, const uint8_t* mask_host,
-                             const double* dval_host)
+static wd_status alloc_impl(wd_grid g)
 {
     const Dims& D = g->D;
     cudaStream_t st = g->stream;
     const long long tot = D.total;
-    // coordinates
     ST(dmalloc(g, (void**)&g->xyz, (size_t)tot * 3 * 8));
     CK(cudaMemsetAsync(g->xyz, 0, (size_t)tot * 3 * 8, st));
+    // line tables
+    for (int d = 0; d < D.ndim; d++) {
+        std::vector<double> a, c;
+        int imp;
+        derivative_rows(g->desc.scheme, D.n[d], D.per[d], a, c, imp);
+        ST(build_line_table(D.n[d], D.per[d], a, c, imp, g->dtab[d]));
+        std::vector<double> z(D.n[d], 0.0);
+        ST(build_line_table(D.n[d], D.per[d], z, z, 0, g->etab[d]));
+    }
+    ST(dmalloc(g, (void**)&g->xi_d, (size_t)tot * 9 * 8));
+    ST(dmalloc(g, (void**)&g->J_d, (size_t)tot * 8));
+    ST(dmalloc(g, (void**)&g->dx_d, (size_t)tot * 3 * 8));
+    CK(cudaMemsetAsync(g->xi_d, 0, (size_t)tot * 9 * 8, st));
+    CK(cudaMemsetAsync(g->dx_d, 0, (size_t)tot * 3 * 8, st));
+    if (sizeof(M) == 8) {
+        g->xi_m = g->xi_d;
+        g->xi_alias = 1;
+    } else {
+        ST(dmalloc(g, &g->xi_m, (size_t)tot * 9 * sizeof(M)));
+        CK(cudaMemsetAsync(g->xi_m, 0, (size_t)tot * 9 * sizeof(M), st));
+        g->xi_alias = 0;
+    }
+    ST(dmalloc(g, &g->sig1, (size_t)tot * sizeof(M)));
+    ST(dmalloc(g, &g->sig2, (size_t)tot * sizeof(M)));
+    ST(dmalloc(g, &g->lads, (size_t)tot * 3 * sizeof(M)));
+    long long fmax = 0;
+    for (int d = 0; d < 3; d++) {
+        long long f = (long long)D.n[(d + 1) % 3] * D.n[(d + 2) % 3];
+        if (f > fmax) fmax = f;
+    }
+    g->fmax = fmax;
+    ST(dmalloc(g, (void**)&g->ffr, (size_t)fmax * 6 * 8));
+    CK(cudaMemsetAsync(g->ffr, 0, (size_t)fmax * 6 * 8, st));
+    // wall faces (Dirichlet 0)
+    ST(dmalloc(g, (void**)&g->wall, (size_t)tot));
+    ST(dmalloc(g, (void**)&g->mask, (size_t)tot));
+    ST(dmalloc(g, &g->dval, (size_t)tot * sizeof(T)));
+    {
+        std::vector<uint8_t> wall((size_t)tot, 0);
+        for (int k = 0; k < D.n[2]; k++)
+            for (int j = 0; j < D.n[1]; j++)
+                for (int i = 0; i < D.n[0]; i++) {
+                    int c[3] = {i, j, k};
+                    bool w = false;
+                    for (int d = 0; d < D.ndim; d++) {
+                        if (c[d] == 0 && g->desc.bc_lo[d] == WD_BC_WALL) w = true;
+                        if (c[d] == D.n[d] - 1 && g->desc.bc_hi[d] == WD_BC_WALL) w = true;
+                    }
+                    wall[(size_t)D.idx(i, j, k)] = w;
+                }
+        CK(cudaMemcpyAsync(g->wall, wall.data(), (size_t)tot, cudaMemcpyHostToDevice, st));
+        CK(cudaStreamSynchronize(st));
+    }
+    ST(dmalloc(g, (void**)&g->dcount, sizeof(unsigned long long)));
+    for (int k = 0; k < W_NWORK; k++) {
+        ST(dmalloc(g, &g->w[k], (size_t)tot * sizeof(T)));
+        CK(cudaMemsetAsync(g->w[k], 0, (size_t)tot * sizeof(T), st));
+    }
+    g->nred = (int)std::min<long long>((tot + 255) / 256, 1024);
+    g->npartial = std::max(g->nred, D.n[0] * D.n[2]);
+    ST(dmalloc(g, (void**)&g->partial, (size_t)g->npartial * 2 * 8));
+    ST(dmalloc(g, (void**)&g->counter, sizeof(unsigned)));
+    ST(dmalloc(g, (void**)&g->result, (size_t)2 * g->batch * 8));
+    CK(cudaMemsetAsync(g->counter, 0, (size_t)sizeof(unsigned), st));
+    CK(cudaMemsetAsync(g->result, 0, (size_t)2 * g->batch * 8, st));
+    if (cudaMallocHost(&g->hres, (size_t)2 * g->batch * sizeof(double)) != cudaSuccess)
+        return set_error(WD_ERR_OOM, "pinned");
+    CK(cudaStreamSynchronize(st));
+    return WD_OK;
+}
+
+// coordinates, metrics (Sec. 3.1), far-field spacing ratios and the Dirichlet set; temporary
+// device memory comes from the stream-ordered allocator, so nothing here waits for other
+// streams
+template <typename T, typename M>
+static wd_status geometry_impl(wd_grid g, const double* xyz_host, const uint8_t* mask_host,
+                               const double* dval_host)
+{
+    const Dims& D = g->D;
+    cudaStream_t st = g->stream;
+    const long long tot = D.total;
+    g->gen++;
+    g->lads_exp = -1.0;
     for (int m = 0; m < D.ndim; m++)
         CK(cudaMemcpy2DAsync(g->xyz + m * tot, (size_t)D.pitch * 8,
                              xyz_host + (size_t)m * D.n[0] * D.n[1] * D.n[2], (size_t)D.n[0] * 8,
                              (size_t)D.n[0] * 8, (size_t)D.n[1] * D.n[2], cudaMemcpyHostToDevice, st));
     // uniform Cartesian 3-D grid?  x = x0 + i hx, y = y0 + j hy, z = z0 + k hz at every node
+    g->cart = 0;
     if (D.ndim == 3) {
         const size_t N = (size_t)D.n[0] * D.n[1] * D.n[2];
         const double* X = xyz_host;
@@ -889,37 +1052,22 @@ static wd_status create_impl(wd_grid g, const double* xyz_host, const uint8_t* m
         g->h[1] = hy;
         g->h[2] = hz;
     }
-    // line tables
-    for (int d = 0; d < D.ndim; d++) {
-        std::vector<double> a, c;
-        int imp;
-        derivative_rows(g->desc.scheme, D.n[d], D.per[d], a, c, imp);
-        ST(build_line_table(D.n[d], D.per[d], a, c, imp, g->dtab[d]));
-        std::vector<double> z(D.n[d], 0.0);
-        ST(build_line_table(D.n[d], D.per[d], z, z, 0, g->etab[d]));
-    }
     // metrics: A[(m*3+l)] = dx_m/dxi_l by the grid's scheme, periodic shift added back
-    ST(dmalloc(g, (void**)&g->xi_d, (size_t)tot * 9 * 8));
-    ST(dmalloc(g, (void**)&g->J_d, (size_t)tot * 8));
-    ST(dmalloc(g, (void**)&g->dx_d, (size_t)tot * 3 * 8));
-    CK(cudaMemsetAsync(g->xi_d, 0, (size_t)tot * 9 * 8, st));
-    CK(cudaMemsetAsync(g->dx_d, 0, (size_t)tot * 3 * 8, st));
-    if (sizeof(M) == 8) {
-        g->xi_m = g->xi_d;
-        g->xi_alias = 1;
-    } else {
-        ST(dmalloc(g, &g->xi_m, (size_t)tot * 9 * sizeof(M)));
-        CK(cudaMemsetAsync(g->xi_m, 0, (size_t)tot * 9 * sizeof(M), st));
-        g->xi_alias = 0;
-    }
-    ST(dmalloc(g, &g->sig1, (size_t)tot * sizeof(M)));
-    ST(dmalloc(g, &g->sig2, (size_t)tot * sizeof(M)));
-    ST(dmalloc(g, &g->lads, (size_t)tot * 3 * sizeof(M)));
     {
         double* A = nullptr;
         double* tmp = nullptr;
-        if (cudaMalloc(&A, (size_t)tot * 9 * 8) != cudaSuccess || cudaMalloc(&tmp, (size_t)tot * 8) != cudaSuccess) {
-            cudaFree(A);
+        if (cudaMallocAsync((void**)&A, (size_t)tot * 9 * 8, st) != cudaSuccess ||
+            cudaMallocAsync((void**)&tmp, (size_t)tot * 8, st) != cudaSuccess) {
+            if (A) cudaFreeAsync(A, st);
+            cudaGetLastError();
+            return set_error(WD_ERR_OOM, "metric scratch");
+        }
+        // WD_FP32: the coordinates are rounded to FP32 and differentiated in FP32
+        const bool f32 = g->desc.precision == WD_FP32;
+        float* fx = nullptr;
+        if (f32 && cudaMallocAsync((void**)&fx, (size_t)tot * 2 * sizeof(float), st) != cudaSuccess) {
+            cudaFreeAsync(A, st);
+            cudaFreeAsync(tmp, st);
             cudaGetLastError();
             return set_error(WD_ERR_OOM, "metric scratch");
         }
@@ -936,98 +1084,66 @@ static wd_status create_impl(wd_grid g, const double* xyz_host, const uint8_t* m
                     ce = launch_unwrap(D, l, src, shift, tmp, st);
                     src = tmp;
                 }
-                Fields<double> f;
-                std::memset(&f, 0, sizeof(f));
-                f.in[0] = src;
-                f.out[0] = A + (long long)(m * 3 + l) * tot;
-                if (ce == cudaSuccess)
-                    ce = launch_line<double, double>(D, l, g->dtab[l], op, 1, 0, f, nullptr, 0, 0, st);
+                double* out = A + (long long)(m * 3 + l) * tot;
+                if (f32) {
+                    Fields<float> f;
+                    std::memset(&f, 0, sizeof(f));
+                    f.in[0] = fx;
+                    f.out[0] = fx + tot;
+                    if (ce == cudaSuccess) ce = launch_convert<double, float>(src, fx, tot, st);
+                    if (ce == cudaSuccess)
+                        ce = launch_line<float, float>(D, l, g->dtab[l], op, 1, 0, f, nullptr, 0, 0, st);
+                    if (ce == cudaSuccess) ce = launch_convert<float, double>(fx + tot, out, tot, st);
+                } else {
+                    Fields<double> f;
+                    std::memset(&f, 0, sizeof(f));
+                    f.in[0] = src;
+                    f.out[0] = out;
+                    if (ce == cudaSuccess)
+                        ce = launch_line<double, double>(D, l, g->dtab[l], op, 1, 0, f, nullptr, 0, 0, st);
+                }
                 // derivative of the removed linear part shift * t / n: shift / n, exact for
                 // every scheme
                 if (ce == cudaSuccess && shift != 0.0)
                     ce = launch_add_const(D, A + (long long)(m * 3 + l) * tot, shift / D.n[l], st);
             }
-        if (ce != cudaSuccess) {
-            cudaFree(A);
-            cudaFree(tmp);
-            return cuda_error(ce, "metric derivatives");
-        }
-        cudaFree(tmp);
-        ce = launch_metric_finish<M>(D, A, g->xi_d, g->J_d, g->dx_d,
-                                     g->xi_alias ? nullptr : (M*)g->xi_m, (M*)g->sig1, (M*)g->sig2, st);
-        cudaStreamSynchronize(st);
-        cudaFree(A);
-        if (ce != cudaSuccess) return cuda_error(ce, "metric finish");
+        if (ce == cudaSuccess)
+            ce = launch_metric_finish<M>(D, A, g->xi_d, g->J_d, g->dx_d,
+                                         g->xi_alias ? nullptr : (M*)g->xi_m, (M*)g->sig1, (M*)g->sig2, st);
+        cudaFreeAsync(A, st);
+        cudaFreeAsync(tmp, st);
+        if (fx) cudaFreeAsync(fx, st);
+        if (ce != cudaSuccess) return cuda_error(ce, "metrics");
     }
-    // far-field spacing ratios
-    long long fmax = 0;
-    for (int d = 0; d < 3; d++) {
-        long long f = (long long)D.n[(d + 1) % 3] * D.n[(d + 2) % 3];
-        if (f > fmax) fmax = f;
-    }
-    g->fmax = fmax;
-    ST(dmalloc(g, (void**)&g->ffr, (size_t)fmax * 6 * 8));
-    CK(cudaMemsetAsync(g->ffr, 0, (size_t)fmax * 6 * 8, st));
-    CK(launch_ff_ratio(D, g->xyz, g->ffr, fmax, st));
+    CK(launch_ff_ratio(D, g->xyz, g->ffr, g->fmax, st));
     // Dirichlet set: wall faces + caller mask
-    ST(dmalloc(g, (void**)&g->wall, (size_t)tot));
-    ST(dmalloc(g, (void**)&g->mask, (size_t)tot));
-    ST(dmalloc(g, &g->dval, (size_t)tot * sizeof(T)));
-    {
-        std::vector<uint8_t> wall((size_t)tot, 0);
-        for (int k = 0; k < D.n[2]; k++)
-            for (int j = 0; j < D.n[1]; j++)
-                for (int i = 0; i < D.n[0]; i++) {
-                    int c[3] = {i, j, k};
-                    bool w = false;
-                    for (int d = 0; d < D.ndim; d++) {
-                        if (c[d] == 0 && g->desc.bc_lo[d] == WD_BC_WALL) w = true;
-                        if (c[d] == D.n[d] - 1 && g->desc.bc_hi[d] == WD_BC_WALL) w = true;
-                    }
-                    wall[(size_t)D.idx(i, j, k)] = w;
-                }
-        CK(cudaMemcpyAsync(g->wall, wall.data(), (size_t)tot, cudaMemcpyHostToDevice, st));
-        CK(cudaStreamSynchronize(st));
-    }
     {
         uint8_t* um = nullptr;
         T* uv = nullptr;
-        size_t Nd = (size_t)D.n[0] * D.n[1] * D.n[2];
+        const size_t Nd = (size_t)D.n[0] * D.n[1] * D.n[2];
         if (mask_host) {
-            if (cudaMalloc(&um, Nd) != cudaSuccess) return set_error(WD_ERR_OOM, "mask upload");
-            cudaMemcpy(um, mask_host, Nd, cudaMemcpyHostToDevice);
+            if (cudaMallocAsync((void**)&um, Nd, st) != cudaSuccess) {
+                cudaGetLastError();
+                return set_error(WD_ERR_OOM, "mask upload");
+            }
+            CK(cudaMemcpyAsync(um, mask_host, Nd, cudaMemcpyHostToDevice, st));
             if (dval_host) {
                 std::vector<T> v(Nd);
                 for (size_t q = 0; q < Nd; q++) v[q] = (T)dval_host[q];
-                if (cudaMalloc(&uv, Nd * sizeof(T)) != cudaSuccess) {
-                    cudaFree(um);
+                if (cudaMallocAsync((void**)&uv, Nd * sizeof(T), st) != cudaSuccess) {
+                    cudaFreeAsync(um, st);
+                    cudaGetLastError();
                     return set_error(WD_ERR_OOM, "dval upload");
                 }
-                cudaMemcpy(uv, v.data(), Nd * sizeof(T), cudaMemcpyHostToDevice);
+                // the staging copy of pageable memory completes before the call returns
+                CK(cudaMemcpyAsync(uv, v.data(), Nd * sizeof(T), cudaMemcpyHostToDevice, st));
             }
         }
         cudaError_t ce = launch_mask_merge<T>(D, um, uv, g->mask, (T*)g->dval, g->wall, st);
-        cudaStreamSynchronize(st);
-        cudaFree(um);
-        cudaFree(uv);
+        if (um) cudaFreeAsync(um, st);
+        if (uv) cudaFreeAsync(uv, st);
         if (ce != cudaSuccess) return cuda_error(ce, "mask merge");
     }
-    ST(dmalloc(g, (void**)&g->dcount, sizeof(unsigned long long)));
-    // work arrays, reduction buffers
-    for (int k = 0; k < W_NWORK; k++) {
-        ST(dmalloc(g, &g->w[k], (size_t)tot * sizeof(T)));
-        CK(cudaMemsetAsync(g->w[k], 0, (size_t)tot * sizeof(T), st));
-    }
-    g->nred = (int)std::min<long long>((tot + 255) / 256, 1024);
-    g->npartial = std::max(g->nred, D.n[0] * D.n[2]);
-    ST(dmalloc(g, (void**)&g->partial, (size_t)g->npartial * 2 * 8));
-    ST(dmalloc(g, (void**)&g->counter, sizeof(unsigned)));
-    ST(dmalloc(g, (void**)&g->result, (size_t)2 * g->batch * 8));
-    CK(cudaMemsetAsync(g->counter, 0, sizeof(unsigned), st));
-    CK(cudaMemsetAsync(g->result, 0, (size_t)2 * g->batch * 8, st));
-    if (cudaMallocHost(&g->hres, (size_t)2 * g->batch * sizeof(double)) != cudaSuccess)
-        return set_error(WD_ERR_OOM, "pinned");
-    CK(cudaStreamSynchronize(st));
     return WD_OK;
 }
 
@@ -1115,7 +1231,8 @@ wd_status wd_create_grid(const wd_grid_desc* desc, const double* xyz_host, const
         s = dispatch(g, [&](auto* t, auto* m) {
             using T = std::remove_pointer_t<decltype(t)>;
             using M = std::remove_pointer_t<decltype(m)>;
-            return create_impl<T, M>(g, xyz_host, mask_host, dval_host);
+            ST(alloc_impl<T, M>(g));
+            return geometry_impl<T, M>(g, xyz_host, mask_host, dval_host);
         });
     }
     if (s == WD_OK) s = count_active(g);
@@ -1181,11 +1298,7 @@ wd_status wd_step_unsteady(wd_grid g, const uint8_t* mask_dev, const void* dval_
     wd_status s = dispatch(g, [&](auto* t, auto* m) {
         using T = std::remove_pointer_t<decltype(t)>;
         using M = std::remove_pointer_t<decltype(m)>;
-        if (mask_dev) {
-            CK(launch_mask_merge<T>(g->D, mask_dev, (const T*)dval_dev, g->mask, (T*)g->dval, g->wall,
-                                    g->stream));
-            ST(count_active(g));
-        }
+        if (mask_dev) ST(update_dirichlet(g, mask_dev, dval_dev));
         Solver<T, M> S(g, p);
         return S.solve(phi_dev, stats, true);
     });
@@ -1332,6 +1445,23 @@ wd_status wd_steps(wd_grid g, const wd_solve_params* p, int kind, void* phi_dev,
     });
 }
 
+wd_status wd_reset_geometry(wd_grid g, const double* xyz_host, const uint8_t* mask_host,
+                            const double* dval_host)
+{
+    if (!g || !xyz_host) return set_error(WD_ERR_INVALID_ARG, "NULL grid or xyz_host");
+    wd_status s;
+    {
+        StreamGuard sg(g);
+        s = dispatch(g, [&](auto* t, auto* m) {
+            using T = std::remove_pointer_t<decltype(t)>;
+            using M = std::remove_pointer_t<decltype(m)>;
+            return geometry_impl<T, M>(g, xyz_host, mask_host, dval_host);
+        });
+    }
+    if (s == WD_OK) s = count_active(g);
+    return s;
+}
+
 wd_status wd_profile(wd_grid g, int enable)
 {
     if (!g) return set_error(WD_ERR_INVALID_ARG, "grid is NULL");
@@ -1356,3 +1486,51 @@ wd_status wd_profile_read(wd_grid g, int cls, double* ms_total, long long* launc
 }
 
 }  // extern "C"
+
+namespace wd {
+
+template <typename T, typename M>
+struct SolveTaskImpl final : SolveTask {
+    wd_solve_params prm;      // the task's own copy; the solver points at it
+    Solver<T, M> S;
+    SolveTaskImpl(wd_grid g, const wd_solve_params* p) : prm(*p), S(g, &prm) {}
+    wd_status begin(const void* phi, bool warm) override { return S.begin(phi, warm); }
+    wd_status enqueue() override { return S.enqueue(); }
+    wd_status complete() override { return S.complete(); }
+    bool finished() const override { return S.finished(); }
+    bool check() const override { return S.R.check; }
+    wd_status finish(void* phi, wd_stats* st) override { return S.finish(phi, st); }
+};
+
+SolveTask* make_solve_task(wd_grid g, const wd_solve_params* p)
+{
+    SolveTask* out = nullptr;
+    dispatch(g, [&](auto* t, auto* m) {
+        using T = std::remove_pointer_t<decltype(t)>;
+        using M = std::remove_pointer_t<decltype(m)>;
+        out = new SolveTaskImpl<T, M>(g, p);
+        return WD_OK;
+    });
+    return out;
+}
+
+cudaStream_t grid_stream(wd_grid g) { return g->stream; }
+cudaStream_t grid_user_stream(wd_grid g) { return g->user_stream; }
+size_t grid_bytes(wd_grid g) { return g->bytes; }
+wd_status check_solve_params(const wd_solve_params* p) { return check_params(p); }
+
+// merges a dense caller mask / Dirichlet values into the grid's Dirichlet set (walls kept)
+// and recounts the active nodes; waits for the grid's stream
+wd_status update_dirichlet(wd_grid g, const uint8_t* mask_dev, const void* dval_dev)
+{
+    wd_status s = dispatch(g, [&](auto* t, auto*) {
+        using T = std::remove_pointer_t<decltype(t)>;
+        CK(launch_mask_merge<T>(g->D, mask_dev, (const T*)dval_dev, g->mask, (T*)g->dval, g->wall,
+                                g->stream));
+        return WD_OK;
+    });
+    if (s != WD_OK) return s;
+    return count_active(g);
+}
+
+}  // namespace wd

@@ -70,6 +70,8 @@ cudaError_t launch_norms(const Dims& D, const T* newp, T* oldp, const uint8_t* m
 template <typename T>
 cudaError_t launch_fill(T* p, long long n, T v, cudaStream_t st);
 
+template <typename S, typename DT>
+cudaError_t launch_convert(const S* in, DT* out, long long n, cudaStream_t st);
 cudaError_t launch_unwrap(const Dims& D, int dir, const double* x, double shift, double* out,
                           cudaStream_t st);
 cudaError_t launch_add_const(const Dims& D, double* p, double c, cudaStream_t st);
@@ -86,5 +88,23 @@ cudaError_t launch_mask_merge(const Dims& D, const uint8_t* src_dense, const T* 
                               uint8_t* mask, T* dval, const uint8_t* wallmask, cudaStream_t st);
 cudaError_t launch_count(const Dims& D, const uint8_t* mask, unsigned long long* out,
                          cudaStream_t st);
+
+// ---- solve tasks for the request loop ------------------------------------------------
+// One solve of wd_solve split into device slices (see Solver::begin .. finish).
+struct SolveTask {
+    virtual ~SolveTask() {}
+    virtual wd_status begin(const void* phi, bool warm) = 0;
+    virtual wd_status enqueue() = 0;        // queues one slice (and its norm copy)
+    virtual wd_status complete() = 0;       // host step after the slice has run
+    virtual bool finished() const = 0;
+    virtual bool check() const = 0;         // the last slice ends at a convergence check
+    virtual wd_status finish(void* phi, wd_stats* stats) = 0;   // queues the copy-out
+};
+SolveTask* make_solve_task(wd_grid g, const wd_solve_params* p);
+cudaStream_t grid_stream(wd_grid g);
+cudaStream_t grid_user_stream(wd_grid g);
+size_t grid_bytes(wd_grid g);
+wd_status check_solve_params(const wd_solve_params* p);
+wd_status update_dirichlet(wd_grid g, const uint8_t* mask_dev, const void* dval_dev);
 
 }  // namespace wd

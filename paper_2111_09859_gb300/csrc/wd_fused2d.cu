@@ -493,7 +493,6 @@ cudaError_t f2_launch(F2Args<T, M> a, int which, cudaStream_t st)
 }
 
 template cudaError_t f2_launch<double, double>(F2Args<double, double>, int, cudaStream_t);
-template cudaError_t f2_launch<float, double>(F2Args<float, double>, int, cudaStream_t);
 template cudaError_t f2_launch<float, float>(F2Args<float, float>, int, cudaStream_t);
 
 }  // namespace wd

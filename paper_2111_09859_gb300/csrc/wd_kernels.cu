@@ -527,6 +527,23 @@ __global__ void k_unwrap(Dims D, int dir, const double* __restrict__ x, double s
     }
 }
 
+template <typename S, typename DT>
+__global__ void k_convert(const S* __restrict__ in, DT* out, long long n)
+{
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+         e += (long long)gridDim.x * blockDim.x)
+        out[e] = DT(in[e]);
+}
+
+template <typename S, typename DT>
+cudaError_t launch_convert(const S* in, DT* out, long long n, cudaStream_t st)
+{
+    k_convert<S, DT><<<pw_grid(n), 256, 0, st>>>(in, out, n);
+    return cudaGetLastError();
+}
+template cudaError_t launch_convert<double, float>(const double*, float*, long long, cudaStream_t);
+template cudaError_t launch_convert<float, double>(const float*, double*, long long, cudaStream_t);
+
 cudaError_t launch_unwrap(const Dims& D, int dir, const double* x, double shift, double* out,
                           cudaStream_t st)
 {
@@ -719,7 +736,7 @@ cudaError_t launch_count(const Dims& D, const uint8_t* mask, unsigned long long*
 }
 
 // ------------------------------------------------------------------------------------
-// explicit instantiations: (state, metric) = (double, double), (float, double), (float, float)
+// explicit instantiations: (state, metric) = (double, double), (float, float)
 // ------------------------------------------------------------------------------------
 
 #define WD_INST_TM(T, M)                                                                          \
@@ -736,7 +753,6 @@ cudaError_t launch_count(const Dims& D, const uint8_t* mask, unsigned long long*
                                                cudaStream_t);
 
 WD_INST_TM(double, double)
-WD_INST_TM(float, double)
 WD_INST_TM(float, float)
 
 #define WD_INST_T(T)                                                                              \

@@ -59,6 +59,10 @@ class Stats(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class ServerConfig(C.Structure):
+    _fields_ = [("max_device_bytes", C.c_size_t), ("max_active", C.c_int), ("pool_per_shape", C.c_int)]
+
+
 _lock = threading.Lock()
 _lib = None
 
@@ -85,6 +89,16 @@ SIGNATURES = {
     "wd_profile": (_i, [_vp, _i]),
     "wd_profile_read": (_i, [_vp, _i, C.POINTER(C.c_double), C.POINTER(C.c_longlong)]),
     "wd_change_norms_noalloc": (_i, [_vp, _vp, _vp, C.c_longlong, _i, _d, _vp, _vp]),
+    "wd_reset_geometry": (_i, [_vp, _vp, _vp, _vp]),
+    "wd_server_create": (_i, [C.POINTER(ServerConfig), C.POINTER(_vp)]),
+    "wd_server_submit": (_i, [_vp, C.POINTER(GridDesc), _vp, _vp, _vp, C.POINTER(SolveParams), _vp,
+                              C.POINTER(C.c_longlong)]),
+    "wd_server_submit_grid": (_i, [_vp, _vp, _vp, _vp, _i, C.POINTER(SolveParams), _vp,
+                                   C.POINTER(C.c_longlong)]),
+    "wd_server_wait": (_i, [_vp, C.c_longlong, _d, C.POINTER(Stats), C.POINTER(C.c_double)]),
+    "wd_server_info": (_i, [_vp, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong),
+                            C.POINTER(C.c_longlong), C.POINTER(C.c_size_t), C.POINTER(C.c_longlong)]),
+    "wd_server_destroy": (None, [_vp]),
 }
 
 K_DERIV, K_DIV, K_FILTER, K_GAUSS, K_POINT, K_BC, K_NORM = range(7)
@@ -137,6 +151,37 @@ def _ptr(t):
     return C.c_void_p(t.data_ptr()) if t is not None else None
 
 
+def _grid_inputs(spec, precision, scheme):
+    """(GridDesc, xyz, mask, dval, n) of a GridSpec-like object, arrays as contiguous numpy."""
+    shape = tuple(int(s) for s in spec.shape)
+    ndim = len(shape)
+    batch = int(getattr(spec, "batch", 1))
+    n = list(shape) + [1] * (3 - ndim)
+    if ndim == 2:
+        n[2] = batch
+    d = GridDesc()
+    d.ndim = ndim
+    for k in range(3):
+        d.n[k] = n[k]
+        d.bc_lo[k] = spec.bc_lo[k] if k < ndim else BC_WALL
+        d.bc_hi[k] = spec.bc_hi[k] if k < ndim else BC_WALL
+        for m in range(3):
+            d.period[k][m] = float(spec.period[k][m]) if spec.period is not None else 0.0
+    d.precision = precision
+    d.scheme = scheme
+    d.L_ref = float(getattr(spec, "L_ref", 1.0))
+    xyz = np.ascontiguousarray(np.asarray(spec.xyz, dtype=np.float64).reshape(ndim, -1))
+    mask = getattr(spec, "mask", None)
+    dval = getattr(spec, "dval", None)
+    mask = None if mask is None else np.ascontiguousarray(mask, dtype=np.uint8).reshape(-1)
+    dval = None if dval is None else np.ascontiguousarray(dval, dtype=np.float64).reshape(-1)
+    return d, xyz, mask, dval, n
+
+
+def _np_ptr(a):
+    return None if a is None else a.ctypes.data
+
+
 class Grid:
     """A structured grid on the GPU (wd_create_grid).
 
@@ -149,38 +194,17 @@ class Grid:
         self.shape = tuple(int(s) for s in spec.shape)
         self.ndim = len(self.shape)
         self.batch = int(getattr(spec, "batch", 1))
-        n = list(self.shape) + [1] * (3 - self.ndim)
-        if self.ndim == 2:
-            n[2] = self.batch
+        d, xyz, mask, dval, n = _grid_inputs(spec, precision, scheme)
         self.n = n
         self.N = n[0] * n[1] * n[2]
         self.precision = precision
         self.scheme = scheme
         self.dtype = torch.float64 if precision == FP64 else torch.float32
-        d = GridDesc()
-        d.ndim = self.ndim
-        for k in range(3):
-            d.n[k] = n[k]
-            d.bc_lo[k] = spec.bc_lo[k] if k < self.ndim else BC_WALL
-            d.bc_hi[k] = spec.bc_hi[k] if k < self.ndim else BC_WALL
-            for m in range(3):
-                d.period[k][m] = float(spec.period[k][m]) if spec.period is not None else 0.0
-        d.precision = precision
-        d.scheme = scheme
-        d.L_ref = float(getattr(spec, "L_ref", 1.0))
         self.desc = d
-        xyz = np.ascontiguousarray(np.asarray(spec.xyz, dtype=np.float64).reshape(self.ndim, -1))
-        mask = getattr(spec, "mask", None)
-        dval = getattr(spec, "dval", None)
-        mask = None if mask is None else np.ascontiguousarray(mask, dtype=np.uint8).reshape(-1)
-        dval = None if dval is None else np.ascontiguousarray(dval, dtype=np.float64).reshape(-1)
         self.stream = stream
         h = C.c_void_p()
-        _check(lib().wd_create_grid(
-            C.byref(d), xyz.ctypes.data,
-            None if mask is None else mask.ctypes.data,
-            None if dval is None else dval.ctypes.data,
-            _stream_handle(stream), C.byref(h)))
+        _check(lib().wd_create_grid(C.byref(d), xyz.ctypes.data, _np_ptr(mask), _np_ptr(dval),
+                                    _stream_handle(stream), C.byref(h)))
         self._h = h
         self._device = torch.device("cuda", torch.cuda.current_device())
 
@@ -194,6 +218,14 @@ class Grid:
             self.close()
         except Exception:
             pass
+
+    def reset_geometry(self, spec):
+        """New coordinates / Dirichlet set of the same shape (wd_reset_geometry)."""
+        d, xyz, mask, dval, n = _grid_inputs(spec, self.precision, self.scheme)
+        if list(n) != list(self.n):
+            raise ValueError("reset_geometry needs the grid's shape")
+        self._sync_stream()
+        _check(lib().wd_reset_geometry(self._h, xyz.ctypes.data, _np_ptr(mask), _np_ptr(dval)))
 
     def _sync_stream(self):
         lib().wd_set_stream(self._h, _stream_handle(self.stream))
@@ -325,3 +357,78 @@ def change_norms_noalloc(new, old, mask=None, scale=1.0, stream=None):
     _check(lib().wd_change_norms_noalloc(_ptr(new), _ptr(old), _ptr(mask), new.numel(), prec,
                                          float(scale), _ptr(out), _stream_handle(stream)))
     return out
+
+
+class Server:
+    """Request loop of the library (wd_server_*): continuous batching of independent solves.
+
+    ``submit(spec, params, out)`` queues a solve of a new grid (the server creates or re-uses
+    one) and returns a ticket; ``submit_grid(grid, params, phi, ...)`` queues a solve on a
+    caller-owned Grid.  ``wait(ticket)`` returns (status, stats dict, latency seconds).
+    Output tensors must stay alive until their request is done."""
+
+    def __init__(self, max_device_bytes=0, max_active=0, pool_per_shape=0):
+        import torch
+
+        cfg = ServerConfig()
+        cfg.max_device_bytes = int(max_device_bytes)
+        cfg.max_active = int(max_active)
+        cfg.pool_per_shape = int(pool_per_shape)
+        h = C.c_void_p()
+        _check(lib().wd_server_create(C.byref(cfg), C.byref(h)))
+        self._h = h
+        self._device = torch.device("cuda", torch.cuda.current_device())
+        self._keep = {}
+
+    def submit(self, spec, params, out=None, precision=FP32_METRIC64, scheme=C6):
+        import torch
+
+        d, xyz, mask, dval, n = _grid_inputs(spec, precision, scheme)
+        if out is None:
+            out = torch.empty(n[0] * n[1] * n[2], device=self._device,
+                              dtype=torch.float64 if precision == FP64 else torch.float32)
+        t = C.c_longlong()
+        _check(lib().wd_server_submit(self._h, C.byref(d), xyz.ctypes.data, _np_ptr(mask),
+                                      _np_ptr(dval), C.byref(params), _ptr(out), C.byref(t)))
+        self._keep[t.value] = out
+        return t.value, out
+
+    def submit_grid(self, grid, params, phi, warm=False, mask=None, dval=None):
+        grid._sync_stream()
+        t = C.c_longlong()
+        _check(lib().wd_server_submit_grid(self._h, grid._h, _ptr(mask), _ptr(dval), int(bool(warm)),
+                                           C.byref(params), _ptr(phi), C.byref(t)))
+        self._keep[t.value] = (phi, mask, dval)
+        return t.value
+
+    def wait(self, ticket, timeout=-1.0):
+        st = Stats()
+        lat = C.c_double()
+        s = lib().wd_server_wait(self._h, int(ticket), float(timeout), C.byref(st), C.byref(lat))
+        if s == ERR_TIMEOUT:
+            return s, None, None
+        self._keep.pop(ticket, None)
+        if s not in (OK, ERR_NOT_CONVERGED):
+            _check(s)
+        d = st.as_dict()
+        d["status"] = s
+        return s, d, lat.value
+
+    def info(self):
+        q, r, dn, pk = C.c_longlong(), C.c_longlong(), C.c_longlong(), C.c_longlong()
+        b = C.c_size_t()
+        _check(lib().wd_server_info(self._h, C.byref(q), C.byref(r), C.byref(dn), C.byref(b), C.byref(pk)))
+        return {"queued": q.value, "running": r.value, "done": dn.value, "admitted_bytes": b.value,
+                "peak_running": pk.value}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().wd_server_destroy(self._h)
+            self._h = None
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
