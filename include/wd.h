@@ -258,6 +258,29 @@ wd_status wd_change_norms_noalloc(const void* new_dev, const void* old_dev,
 wd_status wd_reset_geometry(wd_grid g, const double* xyz_host, const uint8_t* mask_host,
                             const double* dval_host);
 
+/* ---- receding surface (Sec. 5.5) ------------------------------------------------------ */
+
+/* Surface receding by s (the unsteady re-solve, Sec. 5.5).  For every node q of the dense
+ * field phi_dev (n[0]*n[1]*n[2] values of the grid's state precision, updated in place):
+ * phi_dev[q] -= s (the distance to the receded surface where phi was the distance to the
+ * old one, and the warm start of the next solve); mask_dev[q] = 1 where the new
+ * phi_dev[q] <= 0 (burned; nodes already solid hold phi <= 0 and stay solid), else 0; and
+ * dval_dev[q] = max(phi_dev[q], floor) where the mask is set, else 0.  Pass mask, dval and
+ * phi to wd_step_unsteady (or wd_server_submit_grid with warm = 1).  All arrays are
+ * caller-owned device memory; the work is enqueued on the grid's stream.
+ * Errors: WD_ERR_INVALID_ARG for NULL arrays, s < 0 or floor > 0. */
+wd_status wd_recede(wd_grid g, void* phi_dev, double s, double floor, uint8_t* mask_dev,
+                    void* dval_dev);
+
+/* Length of the level set {phi = level} of a single 2-D grid (the burning perimeter when
+ * phi is the wall distance and level = 0 or the burned depth): marching squares over every
+ * cell, with the crossings interpolated linearly along the cell edges in physical
+ * coordinates, ambiguous cells resolved by the mean of the four corners, lengths summed in
+ * double in a fixed order.  phi_dev: dense device field of the grid's precision.
+ * Synchronous; *length receives the sum.  Errors: WD_ERR_INVALID_ARG for a 3-D or stacked
+ * grid or NULL pointers. */
+wd_status wd_level_length(wd_grid g, const void* phi_dev, double level, double* length);
+
 /* ---- request loop (continuous batching of independent solves) ---------------------- */
 
 /* A server owns one scheduler thread on the current device.  Submitted requests wait in

@@ -3,8 +3,10 @@
 TEST INFRASTRUCTURE ONLY.  The oracle is imported by ``tests/``, by
 ``__graft_entry__.smoke()`` and by ``bench.py``'s CPU-baseline / reference leg, and by
 nothing else.  It shares no code with the CUDA path: the arithmetic lives in
-``wd_oracle.c`` (plain C, one thread, double precision); this module only compiles it
-with gcc and marshals numpy arrays through ctypes.
+``wd_oracle.c`` (plain C, one thread, double precision); this module compiles it with gcc
+and marshals numpy arrays through ctypes.  Two small pieces of the unsteady case are plain
+numpy here: the receding-surface update (Sec. 5.5) and the marching-squares length of a
+level set (the burning perimeter).
 
 Parity of every oracle function is pinned by ``tests/test_oracle_*.py`` against things
 other than the oracle itself: closed forms, polynomial exactness, Fourier symbols,
@@ -255,3 +257,71 @@ def filter_coeffs(hw, alpha_f):
     a = np.zeros(6)
     lib().or_filter_coeffs(int(hw), float(alpha_f), a)
     return a[: hw + 1]
+
+
+def recede(phi, s, floor):
+    """Receding surface of Sec. 5.5 (reading: the surface recedes by s into the
+    propellant, so the distance to it is phi - s, which is also the warm start of the next
+    solve; the burned set is {phi - s <= 0}, whose nodes become Dirichlet nodes holding
+    phi - s floored at ``floor``).  Returns (phi - s, mask, dval)."""
+    new = np.asarray(phi, dtype=np.float64) - s
+    mask = (new <= 0.0).astype(np.uint8)
+    dval = np.where(mask == 1, np.maximum(new, floor), 0.0)
+    return new, mask, dval
+
+
+def level_length(x, y, phi, shape, level=0.0, periodic=(False, False), period=None):
+    """Length of {phi = level} on a 2-D structured grid (i fastest) by marching squares:
+    in every cell the zero crossings of phi - level are interpolated linearly along the cell
+    edges (in physical coordinates) and joined; a cell with four crossings is split by the
+    sign of the mean of its corners.  A periodic direction d adds the cells that close the
+    grid (node n-1 to node 0, whose coordinates are shifted by period[d]).  Plain numpy over
+    all cells."""
+    ni, nj = shape
+    v = (np.asarray(phi, dtype=np.float64) - level).reshape(nj, ni)
+    X = np.asarray(x, dtype=np.float64).reshape(nj, ni)
+    Y = np.asarray(y, dtype=np.float64).reshape(nj, ni)
+    per = np.zeros((2, 2)) if period is None else np.asarray(period, dtype=np.float64)[:2, :2]
+    if periodic[0]:
+        v = np.concatenate([v, v[:, :1]], 1)
+        X = np.concatenate([X, X[:, :1] + per[0, 0]], 1)
+        Y = np.concatenate([Y, Y[:, :1] + per[0, 1]], 1)
+    if periodic[1]:
+        v = np.concatenate([v, v[:1, :]], 0)
+        X = np.concatenate([X, X[:1, :] + per[1, 0]], 0)
+        Y = np.concatenate([Y, Y[:1, :] + per[1, 1]], 0)
+    # corners 0 (i, j), 1 (i+1, j), 2 (i+1, j+1), 3 (i, j+1) of every cell
+    def corner(a, k):
+        return {0: a[:-1, :-1], 1: a[:-1, 1:], 2: a[1:, 1:], 3: a[1:, :-1]}[k]
+    V = [corner(v, k).ravel() for k in range(4)]
+    CX = [corner(X, k).ravel() for k in range(4)]
+    CY = [corner(Y, k).ravel() for k in range(4)]
+    neg = [V[k] < 0.0 for k in range(4)]
+    px, py, has = [], [], []
+    for k in range(4):
+        a, b = k, (k + 1) % 4
+        h = neg[a] != neg[b]
+        with np.errstate(divide="ignore", invalid="ignore"):
+            t = np.where(h, V[a] / (V[a] - V[b]), 0.0)
+        px.append(CX[a] + t * (CX[b] - CX[a]))
+        py.append(CY[a] + t * (CY[b] - CY[a]))
+        has.append(h)
+    nc = sum(h.astype(int) for h in has)
+    total = 0.0
+    # two crossings: join them
+    two = nc == 2
+    idx = np.nonzero(two)[0]
+    pts = []
+    for q in idx:
+        ks = [k for k in range(4) if has[k][q]]
+        pts.append(np.hypot(px[ks[1]][q] - px[ks[0]][q], py[ks[1]][q] - py[ks[0]][q]))
+    total += float(np.sum(pts)) if pts else 0.0
+    # saddles
+    for q in np.nonzero(nc == 4)[0]:
+        ctr = 0.25 * (V[0][q] + V[1][q] + V[2][q] + V[3][q])
+        seg = lambda a, b: np.hypot(px[b][q] - px[a][q], py[b][q] - py[a][q])
+        if (ctr < 0.0) == neg[0][q]:
+            total += seg(0, 1) + seg(2, 3)
+        else:
+            total += seg(3, 0) + seg(1, 2)
+    return total

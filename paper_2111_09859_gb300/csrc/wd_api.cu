@@ -783,6 +783,12 @@ struct Solver {
     }
 
     bool finished() const { return R.phase >= 2; }
+    int stall_window() const
+    {
+        int w = 200;
+        for (int d = 0; d < D.ndim; d++) w = std::max(w, 2 * D.n[d]);
+        return w;
+    }
 
     wd_status enqueue()
     {
@@ -840,8 +846,9 @@ struct Solver {
             R.since_best += R.every;
         }
         // FP32 state: the change norm stops falling at the round-off floor; stop when the
-        // best RMS change has not improved by 5 % over 200 steps
-        if (sizeof(T) == 4 && R.have_tol && R.since_best >= 200) {
+        // best RMS change has not improved by 5 % over a window long enough for a front to
+        // cross the grid twice (at most one node per pseudo step): max(200, 2 max_l n_l)
+        if (sizeof(T) == 4 && R.have_tol && R.since_best >= stall_window()) {
             R.s.converged = 1;
             R.s.stalled = 1;
             R.phase = 2;
@@ -1460,6 +1467,43 @@ wd_status wd_reset_geometry(wd_grid g, const double* xyz_host, const uint8_t* ma
     }
     if (s == WD_OK) s = count_active(g);
     return s;
+}
+
+wd_status wd_recede(wd_grid g, void* phi_dev, double s, double floor, uint8_t* mask_dev,
+                    void* dval_dev)
+{
+    if (!g || !phi_dev || !mask_dev || !dval_dev) return set_error(WD_ERR_INVALID_ARG, "NULL argument");
+    if (!(s >= 0.0) || !(floor <= 0.0)) return set_error(WD_ERR_INVALID_ARG, "need s >= 0 and floor <= 0");
+    StreamGuard sg(g);
+    const long long n = (long long)g->D.n[0] * g->D.n[1] * g->D.n[2];
+    return dispatch(g, [&](auto* t, auto*) {
+        using T = std::remove_pointer_t<decltype(t)>;
+        CK(launch_recede<T>((T*)phi_dev, n, s, floor, mask_dev, (T*)dval_dev, g->stream));
+        return WD_OK;
+    });
+}
+
+wd_status wd_level_length(wd_grid g, const void* phi_dev, double level, double* length)
+{
+    if (!g || !phi_dev || !length) return set_error(WD_ERR_INVALID_ARG, "NULL argument");
+    if (g->D.ndim != 2 || g->batch != 1) return set_error(WD_ERR_INVALID_ARG, "single 2-D grids only");
+    StreamGuard sg(g);
+    const long long cells = (long long)(g->D.n[0] - !g->D.per[0]) * (g->D.n[1] - !g->D.per[1]);
+    const int nb = (int)std::max<long long>(1, std::min<long long>((cells + 255) / 256, g->npartial));
+    wd_status r = dispatch(g, [&](auto* t, auto*) {
+        using T = std::remove_pointer_t<decltype(t)>;
+        CK(launch_level_length<T>(g->D, (const T*)phi_dev, g->xyz, g->desc.period, level, g->partial,
+                                  nb, g->stream));
+        return WD_OK;
+    });
+    if (r != WD_OK) return r;
+    std::vector<double> part(nb);
+    CK(cudaMemcpyAsync(part.data(), g->partial, (size_t)nb * sizeof(double), cudaMemcpyDeviceToHost, g->stream));
+    CK(cudaStreamSynchronize(g->stream));
+    double sum = 0.0;
+    for (int b = 0; b < nb; b++) sum += part[b];
+    *length = sum;
+    return WD_OK;
 }
 
 wd_status wd_profile(wd_grid g, int enable)

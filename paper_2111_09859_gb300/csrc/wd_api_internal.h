@@ -70,6 +70,13 @@ cudaError_t launch_norms(const Dims& D, const T* newp, T* oldp, const uint8_t* m
 template <typename T>
 cudaError_t launch_fill(T* p, long long n, T v, cudaStream_t st);
 
+template <typename T>
+cudaError_t launch_recede(T* phi, long long n, double s, double floor, uint8_t* mask, T* dval,
+                          cudaStream_t st);
+template <typename T>
+cudaError_t launch_level_length(const Dims& D, const T* phi, const double* xyz,
+                                const double (*period)[3], double level, double* part, int nblocks,
+                                cudaStream_t st);
 template <typename S, typename DT>
 cudaError_t launch_convert(const S* in, DT* out, long long n, cudaStream_t st);
 cudaError_t launch_unwrap(const Dims& D, int dir, const double* x, double shift, double* out,

@@ -90,6 +90,8 @@ SIGNATURES = {
     "wd_profile_read": (_i, [_vp, _i, C.POINTER(C.c_double), C.POINTER(C.c_longlong)]),
     "wd_change_norms_noalloc": (_i, [_vp, _vp, _vp, C.c_longlong, _i, _d, _vp, _vp]),
     "wd_reset_geometry": (_i, [_vp, _vp, _vp, _vp]),
+    "wd_recede": (_i, [_vp, _vp, _d, _d, _vp, _vp]),
+    "wd_level_length": (_i, [_vp, _vp, _d, C.POINTER(C.c_double)]),
     "wd_server_create": (_i, [C.POINTER(ServerConfig), C.POINTER(_vp)]),
     "wd_server_submit": (_i, [_vp, C.POINTER(GridDesc), _vp, _vp, _vp, C.POINTER(SolveParams), _vp,
                               C.POINTER(C.c_longlong)]),
@@ -226,6 +228,23 @@ class Grid:
             raise ValueError("reset_geometry needs the grid's shape")
         self._sync_stream()
         _check(lib().wd_reset_geometry(self._h, xyz.ctypes.data, _np_ptr(mask), _np_ptr(dval)))
+
+    def recede(self, phi, s, floor):
+        """Surface receded by s (wd_recede): phi is shifted by -s in place (the warm start of
+        the next solve); returns (mask uint8 tensor, dval tensor)."""
+        import torch
+
+        mask = torch.empty(self.N, dtype=torch.uint8, device=self._device)
+        dval = self.empty()
+        self._sync_stream()
+        _check(lib().wd_recede(self._h, _ptr(phi), float(s), float(floor), _ptr(mask), _ptr(dval)))
+        return mask, dval
+
+    def level_length(self, phi, level=0.0):
+        out = C.c_double()
+        self._sync_stream()
+        _check(lib().wd_level_length(self._h, _ptr(phi), float(level), C.byref(out)))
+        return out.value
 
     def _sync_stream(self):
         lib().wd_set_stream(self._h, _stream_handle(self.stream))

@@ -194,3 +194,113 @@ def stack(specs):
     return GridSpec(first.name + f"x{len(specs)}", first.shape, xyz, first.bc_lo, first.bc_hi,
                     period=first.period, L_ref=first.L_ref, mask=mask, dval=dval,
                     meta=dict(members=[s.meta for s in specs]), batch=len(specs))
+
+
+# ---- star-shaped propellant port (Sec. 5.5) ------------------------------------------
+
+def star_geometry(r_tip: float = 0.45, r_valley: float = 0.2, points: int = 6, fillet: float = 0.03):
+    """Filleted star: `points` tips at r_tip (theta = k 2pi/points) and valleys at r_valley
+    in between, joined by straight edges, every corner replaced by the tangent arc of radius
+    `fillet`.  Returns a dict with the segments [(p, q)], the arcs [(centre, start angle,
+    sweep)] in boundary order, the polygon vertices and the exact perimeter."""
+    nv = 2 * points
+    ang = np.pi * np.arange(nv) / points
+    rad = np.where(np.arange(nv) % 2 == 0, r_tip, r_valley)
+    V = np.stack([rad * np.cos(ang), rad * np.sin(ang)], 1)
+    tin, tout, arcs = [], [], []
+    for k in range(nv):
+        P, A, B = V[k], V[k - 1], V[(k + 1) % nv]
+        u1 = (A - P) / np.linalg.norm(A - P)
+        u2 = (B - P) / np.linalg.norm(B - P)
+        beta = np.arccos(np.clip(u1 @ u2, -1.0, 1.0))       # angle between the two edges
+        t = fillet / np.tan(beta / 2)
+        bis = (u1 + u2) / np.linalg.norm(u1 + u2)
+        c = P + bis * fillet / np.sin(beta / 2)
+        p1, p2 = P + t * u1, P + t * u2                      # tangent points (in, out)
+        a1 = np.arctan2(*(p1 - c)[::-1])
+        a2 = np.arctan2(*(p2 - c)[::-1])
+        sweep = (a2 - a1 + np.pi) % (2 * np.pi) - np.pi      # minor arc, signed
+        tin.append(p1)
+        tout.append(p2)
+        arcs.append((c, a1, sweep))
+    segs = [(tout[k], tin[(k + 1) % nv]) for k in range(nv)]
+    length = sum(np.linalg.norm(q - p) for p, q in segs) + sum(fillet * abs(s) for _, _, s in arcs)
+    return dict(vertices=V, segments=segs, arcs=arcs, fillet=fillet, perimeter=float(length),
+                r_tip=r_tip, r_valley=r_valley, points=points)
+
+
+def _inside_polygon_star(x, y, V):
+    """Points strictly inside the star-shaped (about the origin) polygon V."""
+    nv = len(V)
+    th = np.mod(np.arctan2(y, x), 2 * np.pi)
+    k = np.minimum((th / (2 * np.pi / nv)).astype(np.int64), nv - 1)
+    A, B = V[k], V[(k + 1) % nv]
+    # ray from the origin at angle th meets edge A-B at parameter r
+    dx, dy = np.cos(th), np.sin(th)
+    ex, ey = B[:, 0] - A[:, 0], B[:, 1] - A[:, 1]
+    den = dx * ey - dy * ex
+    r = (A[:, 0] * ey - A[:, 1] * ex) / den
+    return np.hypot(x, y) < r
+
+
+def star_signed_distance(x, y, geom):
+    """Exact distance to the filleted star boundary, negative inside the star (the port),
+    positive in the propellant."""
+    x = np.asarray(x, dtype=np.float64)
+    y = np.asarray(y, dtype=np.float64)
+    d = np.full(x.shape, np.inf)
+    for p, q in geom["segments"]:
+        e = q - p
+        t = np.clip(((x - p[0]) * e[0] + (y - p[1]) * e[1]) / (e @ e), 0.0, 1.0)
+        d = np.minimum(d, np.hypot(x - p[0] - t * e[0], y - p[1] - t * e[1]))
+    rho = geom["fillet"]
+    for c, a1, sw in geom["arcs"]:
+        r = np.hypot(x - c[0], y - c[1])
+        a = np.arctan2(y - c[1], x - c[0])
+        rel = (a - a1) * np.sign(sw)
+        rel = np.mod(rel, 2 * np.pi)
+        on = rel <= abs(sw)
+        e1 = c + rho * np.array([np.cos(a1), np.sin(a1)])
+        e2 = c + rho * np.array([np.cos(a1 + sw), np.sin(a1 + sw)])
+        dend = np.minimum(np.hypot(x - e1[0], y - e1[1]), np.hypot(x - e2[0], y - e2[1]))
+        d = np.minimum(d, np.where(on, np.abs(r - rho), dend))
+    inside = _inside_polygon_star(x, y, geom["vertices"])
+    # corner slivers: a tip fillet removes the part of the polygon beyond its arc, a valley
+    # fillet adds the part of the outside beyond its arc
+    V = geom["vertices"]
+    for k, (c, a1, sw) in enumerate(geom["arcs"]):
+        P = V[k]
+        p1 = c + rho * np.array([np.cos(a1), np.sin(a1)])
+        p2 = c + rho * np.array([np.cos(a1 + sw), np.sin(a1 + sw)])
+        tri = _in_triangle(x, y, P, p1, p2)
+        beyond = tri & (np.hypot(x - c[0], y - c[1]) > rho)
+        if k % 2 == 0:
+            inside &= ~beyond
+        else:
+            inside |= beyond
+    return np.where(inside, -d, d)
+
+
+def _in_triangle(x, y, a, b, c):
+    def side(p, q):
+        return (q[0] - p[0]) * (y - p[1]) - (q[1] - p[1]) * (x - p[0])
+    s1, s2, s3 = side(a, b), side(b, c), side(c, a)
+    return ((s1 >= 0) & (s2 >= 0) & (s3 >= 0)) | ((s1 <= 0) & (s2 <= 0) & (s3 <= 0))
+
+
+def star(n: int = 1025, geom=None, band: int = 3) -> GridSpec:
+    """Star-shaped port on the Cartesian box [-1, 1]^2 with n x n nodes (h = 2/(n-1)).  The
+    box edges take the paper's zero-gradient far-field condition (Sec. 3.5): with outflow
+    extrapolation on all four edges the nearly inviscid LAD solve grows a mode from the box
+    corners.  Solid (port) nodes are Dirichlet: phi = signed distance (negative) within
+    `band` cells of the interface, clamped at -band h deeper in."""
+    geom = geom or star_geometry()
+    x = -1.0 + 2.0 * np.arange(n) / (n - 1)
+    xyz = _cartesian(x, x)
+    h = 2.0 / (n - 1)
+    sd = star_signed_distance(xyz[0], xyz[1], geom)
+    mask = (sd <= 0.0).astype(np.uint8)
+    dval = np.where(mask == 1, np.maximum(sd, -band * h), 0.0)
+    return GridSpec("star", (n, n), xyz, (NEUMANN, NEUMANN), (NEUMANN, NEUMANN),
+                    uniform_h=(h, h), mask=mask, dval=dval,
+                    meta=dict(geom=geom, h=h, band=band, signed_distance=sd))
