@@ -82,6 +82,7 @@ struct wd_grid_s {
     int nred = 0;
     int npartial = 0;           // capacity of `partial` in blocks
     int force_generic = 0;      // WD_FORCE_GENERIC=1 at creation: never use the fused path
+    int part_off = 0;           // WD_PART_OFF=1 at creation: fused 2-D path with PCR passes
     int cart = 0;               // uniform Cartesian 3-D grid (diagonal constant metrics)
     double h[3] = {0, 0, 0};    // its spacings
     HostLineTab dtab[3], ftab[3], etab[3];
@@ -535,6 +536,54 @@ struct Solver {
         return a;
     }
 
+    // the warp partition passes apply when every line length of the grid has tables
+    bool part2d(const F2Args<T, M>& a) const
+    {
+        if (g->force_generic || g->part_off) return false;
+        for (int d = 0; d < 2; d++) {
+            const PartTab<T> dt = g->dtab[d].template pview<T>();
+            if (!p2_supported(a, dt, F2_DERIV, d) || !p2_supported(a, dt, F2_DIV, d)) return false;
+            if (p->filter) {
+                const PartTab<T> ft = g->ftab[d].template pview<T>();
+                if (!p2_supported(a, ft, d == 0 ? P2_FILTER0 : F2_FILTER, d)) return false;
+            }
+        }
+        return true;
+    }
+
+    wd_status step_part2d(F2Args<T, M>& a)
+    {
+        const PartTab<T> dt0 = g->dtab[0].template pview<T>(), dt1 = g->dtab[1].template pview<T>();
+        for (int s = 0; s < 4; s++) {
+            a.src = s == 0 ? W(W_PHIN) : W(W_PHIS);
+            a.dst = W(W_PHIS);
+            a.stage = s;
+            {
+                ProfScope ps(g, WD_K_DERIV);
+                CK(p2_launch<T, M>(a, dt0, F2_DERIV, 0, st));
+                CK(p2_launch<T, M>(a, dt1, F2_DERIV, 1, st));
+            }
+            {
+                ProfScope ps(g, WD_K_DIV);
+                CK(p2_launch<T, M>(a, dt0, F2_DIV, 0, st));
+                CK(p2_launch<T, M>(a, dt1, F2_DIV, 1, st));
+            }
+            {
+                ProfScope ps(g, WD_K_POINT);
+                CK(f2_launch<T, M>(a, F2_STAGE, st));
+            }
+        }
+        a.src = W(W_PHIS);
+        a.dst = W(W_PHIS);
+        if (p->filter) {
+            ProfScope ps(g, WD_K_FILTER);
+            CK(p2_launch<T, M>(a, g->ftab[0].template pview<T>(), P2_FILTER0, 0, st));
+        }
+        ProfScope ps(g, WD_K_NORM);
+        CK(p2_launch<T, M>(a, g->ftab[1].template pview<T>(), F2_FILTER, 1, st));
+        return WD_OK;
+    }
+
     wd_status step_fused(bool poisson)
     {
         if (p->filter) ST(ensure_filter(p->alpha_f));
@@ -545,6 +594,7 @@ struct Solver {
             ST(op_filter(p->alpha_f, op));
             std::memcpy(a.fa, op.fa, sizeof(a.fa));
         }
+        if (part2d(a)) return step_part2d(a);
         for (int s = 0; s < 4; s++) {
             a.src = s == 0 ? W(W_PHIN) : W(W_PHIS);
             a.dst = W(W_PHIS);
@@ -1231,6 +1281,8 @@ wd_status wd_create_grid(const wd_grid_desc* desc, const double* xyz_host, const
     {
         const char* fg = std::getenv("WD_FORCE_GENERIC");
         g->force_generic = fg && fg[0] == '1';
+        const char* po = std::getenv("WD_PART_OFF");
+        g->part_off = po && po[0] == '1';
     }
     wd_status s;
     {

@@ -5,7 +5,7 @@
 
 namespace wd {
 
-enum { F2_DERIV = 0, F2_DIV = 1, F2_STAGE = 2, F2_FILTER = 3 };
+enum { F2_DERIV = 0, F2_DIV = 1, F2_STAGE = 2, F2_FILTER = 3, P2_FILTER0 = 4 };
 
 template <typename T, typename M>
 struct F2Args {
@@ -44,5 +44,13 @@ struct F2Args {
 
 template <typename T, typename M>
 cudaError_t f2_launch(F2Args<T, M> a, int which, cudaStream_t st);
+
+// the same passes with the warp partition solve (wd_part2d.cu), one direction per launch:
+// F2_DERIV, F2_DIV, P2_FILTER0 (filter src into dst) or F2_FILTER (direction 1: filter,
+// line boundary conditions, change norms, commit)
+template <typename T, typename M>
+cudaError_t p2_launch(const F2Args<T, M>& a, const PartTab<T>& tb, int which, int dir, cudaStream_t st);
+template <typename T, typename M>
+bool p2_supported(const F2Args<T, M>& a, const PartTab<T>& tb, int which, int dir);
 
 }  // namespace wd

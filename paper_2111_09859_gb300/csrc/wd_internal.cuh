@@ -56,6 +56,21 @@ struct LineTab {
     T a0, inv_den;
 };
 
+// The same system prepared for the warp partition solve (wd_part2d.cu): a line of N <= 32 R
+// rows (rows N .. 32R-1 are decoupled identity rows) is split into 32 blocks of R rows, one
+// per lane.  The first R-1 rows of a block are eliminated locally (Thomas factors la, iw, g)
+// in terms of the last rows of the previous block and of the block itself (the
+// separators): x = y + P s_prev + Q s.  The 32 separators form a tridiagonal (cyclic when
+// periodic) system solved by five PCR levels over warp shuffles.
+//   loc[(c * (R-1) + k) * 32 + lane], c = 0 la, 1 iw, 2 g, 3 P, 4 Q
+//   sep[c * 32 + lane], c = 0 a_sep, 1 c_sep, 2..6 alpha of levels 0..4, 7..11 gamma, 12 1/b
+template <typename T>
+struct PartTab {
+    int R, N, per, implicit, ok;
+    const T* loc;
+    const T* sep;
+};
+
 enum { OPK_DERIV = 0, OPK_FILTER = 1, OPK_GAUSS = 2 };
 
 struct LineOp {
@@ -82,8 +97,28 @@ struct HostLineTab {
     size_t bytes = 0;
     double key = 0.0;         // alpha_f the table was built for (filters)
     int valid = 0;
+    // partition tables (pok = 0 when the line is not supported: N > 1024, R < 2, or a
+    // periodic N that is not 32 R)
+    int pR = 0, pok = 0;
+    double* pdtab = nullptr;
+    float* pftab = nullptr;
     template <typename T>
     LineTab<T> view() const;
+    template <typename T>
+    PartTab<T> pview() const
+    {
+        PartTab<T> t;
+        const int m = pR - 1;
+        const T* base = sizeof(T) == 8 ? (const T*)(const void*)pdtab : (const T*)(const void*)pftab;
+        t.R = pR;
+        t.N = N;
+        t.per = periodic;
+        t.implicit = implicit;
+        t.ok = pok;
+        t.loc = base;
+        t.sep = base + (size_t)5 * (m > 0 ? m : 0) * 32;
+        return t;
+    }
 };
 
 }  // namespace wd

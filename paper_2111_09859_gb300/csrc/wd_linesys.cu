@@ -119,6 +119,9 @@ static void thomas_host(int n, const std::vector<double>& a, const std::vector<d
     for (int i = n - 2; i >= 0; i--) x[i] = dp[i] - cp[i] * x[i + 1];
 }
 
+static void build_part_table(int N, int periodic, const std::vector<double>& a0v,
+                             const std::vector<double>& c0v, int implicit, HostLineTab& tab);
+
 // Builds the PCR tables of the system a_t x_{t-1} + x_t + c_t x_{t+1} = d_t
 // (periodic: a_0 couples x_{N-1} and c_{N-1} couples x_0).
 wd_status build_line_table(int N, int periodic, const std::vector<double>& a0v,
@@ -227,6 +230,7 @@ wd_status build_line_table(int N, int periodic, const std::vector<double>& a0v,
         return set_error(WD_ERR_CUDA, "upload of a line-solve table failed");
     }
     tab.valid = 1;
+    build_part_table(N, periodic, a0v, c0v, implicit, tab);
     return WD_OK;
 }
 
@@ -234,10 +238,172 @@ void free_line_table(HostLineTab& tab)
 {
     if (tab.dtab) cudaFree(tab.dtab);
     if (tab.ftab) cudaFree(tab.ftab);
+    if (tab.pdtab) cudaFree(tab.pdtab);
+    if (tab.pftab) cudaFree(tab.pftab);
     tab.dtab = nullptr;
     tab.ftab = nullptr;
+    tab.pdtab = nullptr;
+    tab.pftab = nullptr;
     tab.valid = 0;
+    tab.pok = 0;
     tab.bytes = 0;
+}
+
+// rows per lane of the partition solve for a line of N rows (0: not supported)
+int part_rows(int N, int periodic)
+{
+    static const int Rs[] = {3, 4, 5, 8, 9, 16, 17, 32};
+    for (int R : Rs) {
+        if (periodic ? N == 32 * R : N <= 32 * R) return R;
+    }
+    return 0;
+}
+
+// Partition tables of the system a_t x_{t-1} + x_t + c_t x_{t+1} = d_t (periodic: a_0
+// couples x_{N-1}, c_{N-1} couples x_0), checked against a direct solve by emulating the
+// device algorithm on the host; on any mismatch the line falls back to the PCR passes.
+static void build_part_table(int N, int periodic, const std::vector<double>& a0v,
+                             const std::vector<double>& c0v, int implicit, HostLineTab& tab)
+{
+    tab.pok = 0;
+    const int R = part_rows(N, periodic);
+    if (R < 2) return;
+    tab.pR = R;
+    const int NP = 32 * R, m = R - 1;
+    // full rows, identity padding
+    std::vector<double> A(NP, 0.0), B(NP, 1.0), Cc(NP, 0.0);
+    for (int i = 0; i < N; i++) {
+        A[i] = implicit ? a0v[i] : 0.0;
+        Cc[i] = implicit ? c0v[i] : 0.0;
+    }
+    if (!periodic) {
+        A[0] = 0.0;
+        Cc[N - 1] = 0.0;
+    }
+    std::vector<double> loc((size_t)5 * m * 32, 0.0), sep((size_t)13 * 32, 0.0);
+    auto L = [&](int c, int k, int lane) -> double& { return loc[((size_t)c * m + k) * 32 + lane]; };
+    auto S = [&](int c, int lane) -> double& { return sep[(size_t)c * 32 + lane]; };
+    std::vector<double> Pf(32), Pl(32), Qf(32), Ql(32);   // P, Q at the first / last interior row
+    for (int l = 0; l < 32; l++) {
+        const int r0 = l * R;
+        std::vector<double> w(m), g(m), P(m), Q(m);
+        for (int k = 0; k < m; k++) {
+            const int i = r0 + k;
+            const double ak = k > 0 ? A[i] : 0.0;
+            w[k] = B[i] - (k > 0 ? ak * g[k - 1] : 0.0);
+            g[k] = (k < m - 1 ? Cc[i] : 0.0) / w[k];
+            L(0, k, l) = ak;
+            L(1, k, l) = 1.0 / w[k];
+            L(2, k, l) = g[k];
+        }
+        // P = T^-1 (-a_{r0} e_0), Q = T^-1 (-c_{r0+m-1} e_{m-1}) by the same factors
+        auto tsolve = [&](std::vector<double> r, std::vector<double>& x) {
+            std::vector<double> z(m);
+            for (int k = 0; k < m; k++) z[k] = (r[k] - (k > 0 ? L(0, k, l) * z[k - 1] : 0.0)) / w[k];
+            x.assign(m, 0.0);
+            x[m - 1] = z[m - 1];
+            for (int k = m - 2; k >= 0; k--) x[k] = z[k] - g[k] * x[k + 1];
+        };
+        std::vector<double> e(m, 0.0);
+        e[0] = -A[r0];
+        tsolve(e, P);
+        std::fill(e.begin(), e.end(), 0.0);
+        e[m - 1] = -Cc[r0 + m - 1];
+        tsolve(e, Q);
+        for (int k = 0; k < m; k++) {
+            L(3, k, l) = P[k];
+            L(4, k, l) = Q[k];
+        }
+        Pf[l] = P[0];
+        Pl[l] = P[m - 1];
+        Qf[l] = Q[0];
+        Ql[l] = Q[m - 1];
+    }
+    // reduced system of the separators s_l = x_{lR + R - 1}
+    std::vector<double> M(32 * 32, 0.0);
+    for (int l = 0; l < 32; l++) {
+        const int sg = l * R + R - 1, ln = (l + 1) & 31;
+        const double as = A[sg], cs = Cc[sg];
+        S(0, l) = as;
+        S(1, l) = cs;
+        M[l * 32 + ((l + 31) & 31)] += as * Pl[l];
+        M[l * 32 + l] += B[sg] + as * Ql[l] + cs * Pf[ln];
+        M[l * 32 + ln] += cs * Qf[ln];
+    }
+    for (int lev = 0; lev < 5; lev++) {
+        const int h = 1 << lev;
+        std::vector<double> Mn(M);
+        for (int l = 0; l < 32; l++) {
+            const int lm = (l - h) & 31, lp = (l + h) & 31;
+            const double al = -M[l * 32 + lm] / M[lm * 32 + lm];
+            const double ga = lm == lp ? 0.0 : -M[l * 32 + lp] / M[lp * 32 + lp];
+            S(2 + lev, l) = al;
+            S(7 + lev, l) = ga;
+            for (int c = 0; c < 32; c++) Mn[l * 32 + c] = M[l * 32 + c] + al * M[lm * 32 + c] + ga * M[lp * 32 + c];
+        }
+        M = Mn;
+    }
+    for (int l = 0; l < 32; l++) {
+        for (int c = 0; c < 32; c++)
+            if (c != l && std::fabs(M[l * 32 + c]) > 1e-13 * std::fabs(M[l * 32 + l])) return;
+        S(12, l) = 1.0 / M[l * 32 + l];
+    }
+    // emulate the device solve on a deterministic right-hand side and compare
+    std::vector<double> r(NP, 0.0), x(NP, 0.0);
+    for (int i = 0; i < N; i++) r[i] = std::sin(0.37 * i + 0.1) + 0.25 * std::cos(1.91 * i);
+    {
+        std::vector<double> y(NP), D(32), s(32);
+        for (int l = 0; l < 32; l++) {
+            const int r0 = l * R;
+            for (int k = 0; k < m; k++) y[r0 + k] = (r[r0 + k] - L(0, k, l) * (k ? y[r0 + k - 1] : 0.0)) * L(1, k, l);
+            for (int k = m - 2; k >= 0; k--) y[r0 + k] -= L(2, k, l) * y[r0 + k + 1];
+        }
+        for (int l = 0; l < 32; l++) {
+            const int ln = (l + 1) & 31;
+            D[l] = r[l * R + R - 1] - S(0, l) * y[l * R + m - 1] - S(1, l) * y[ln * R];
+        }
+        for (int lev = 0; lev < 5; lev++) {
+            const int h = 1 << lev;
+            std::vector<double> Dn(32);
+            for (int l = 0; l < 32; l++)
+                Dn[l] = D[l] + S(2 + lev, l) * D[(l - h) & 31] + S(7 + lev, l) * D[(l + h) & 31];
+            D = Dn;
+        }
+        for (int l = 0; l < 32; l++) s[l] = D[l] * S(12, l);
+        for (int l = 0; l < 32; l++) {
+            const double sp = s[(l + 31) & 31];
+            for (int k = 0; k < m; k++) x[l * R + k] = y[l * R + k] + L(3, k, l) * sp + L(4, k, l) * s[l];
+            x[l * R + R - 1] = s[l];
+        }
+    }
+    // residual of the full system
+    double res = 0.0, sc = 0.0;
+    for (int i = 0; i < NP; i++) {
+        const double xm = i > 0 ? x[i - 1] : (periodic ? x[NP - 1] : 0.0);
+        const double xp = i < NP - 1 ? x[i + 1] : (periodic ? x[0] : 0.0);
+        res = std::max(res, std::fabs(A[i] * xm + B[i] * x[i] + Cc[i] * xp - r[i]));
+        sc = std::max(sc, std::fabs(r[i]));
+    }
+    for (int i = N; i < NP; i++) res = std::max(res, std::fabs(x[i]));
+    if (!(res <= 1e-12 * (sc > 0 ? sc : 1.0))) return;
+    const size_t nd = loc.size() + sep.size();
+    std::vector<double> h(nd);
+    std::copy(loc.begin(), loc.end(), h.begin());
+    std::copy(sep.begin(), sep.end(), h.begin() + loc.size());
+    std::vector<float> hf(nd);
+    for (size_t i = 0; i < nd; i++) hf[i] = (float)h[i];
+    if (cudaMalloc(&tab.pdtab, nd * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&tab.pftab, nd * sizeof(float)) != cudaSuccess) {
+        cudaGetLastError();
+        return;
+    }
+    if (cudaMemcpy(tab.pdtab, h.data(), nd * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(tab.pftab, hf.data(), nd * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaGetLastError();
+        return;
+    }
+    tab.bytes += nd * (sizeof(double) + sizeof(float));
+    tab.pok = 1;
 }
 
 template <typename T>

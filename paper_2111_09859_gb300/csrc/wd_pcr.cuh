@@ -81,6 +81,7 @@ __device__ __forceinline__ void slots_init(Slot (&q)[R], const LineMap& mp, cons
 // read-only view of one line in shared memory: node j at F[base + j * si]
 template <typename T>
 struct LineView {
+    using value_type = T;
     const T* F;
     int base, si, N, per;
     __device__ __forceinline__ T at(int j) const   // 0 <= j < N, or wrapped when periodic
@@ -111,9 +112,10 @@ __device__ __forceinline__ LineView<T> view_of(const T* F, const Slot& q, const 
 // first derivative row at node i (explicit value, or the right-hand side of a compact row);
 // Sec. 3.2.2, Eq. 16.  Non-periodic ends: one-sided (-25,48,-36,16,-3)/12 at the end node,
 // centred (f_2 - f_0)/2 at the next node; E6 uses E4 at the third node.
-template <typename T>
-__device__ __forceinline__ T deriv_rhs(const LineView<T>& v, int i, int sch)
+template <typename V>
+__device__ __forceinline__ typename V::value_type deriv_rhs(const V& v, int i, int sch)
 {
+    using T = typename V::value_type;
     const int N = v.N;
     if (!v.per) {
         if (i == 0)
@@ -142,9 +144,11 @@ __device__ __forceinline__ T deriv_rhs(const LineView<T>& v, int i, int sch)
 // matrix amplifies high-frequency rounding by up to (1 + 2 alpha) / (1 - 2 alpha)).
 // cf[hw][m] holds a_m/2 - alpha [m == 1] of the order-2hw member; the order drops to
 // 2 hw = 2 x (distance to a non-periodic end), and end nodes are not filtered (Sec. 3.4).
-template <typename T>
-__device__ __forceinline__ T filter_rhs(const LineView<T>& v, int i, const T (*cf)[6])
+template <typename V>
+__device__ __forceinline__ typename V::value_type filter_rhs(const V& v, int i,
+                                                             const typename V::value_type (*cf)[6])
 {
+    using T = typename V::value_type;
     int hw = 5;
     if (!v.per) {
         const int e = i < v.N - 1 - i ? i : v.N - 1 - i;
@@ -160,9 +164,10 @@ __device__ __forceinline__ T filter_rhs(const LineView<T>& v, int i, const T (*c
 }
 
 // truncated 9-point Gaussian of Kawai & Lele's LAD, even reflection at non-periodic ends
-template <typename T>
-__device__ __forceinline__ T gauss_rhs(const LineView<T>& v, int i)
+template <typename V>
+__device__ __forceinline__ typename V::value_type gauss_rhs(const V& v, int i)
 {
+    using T = typename V::value_type;
     return T(3565.0 / 10368.0) * v.at(i) + T(3091.0 / 12960.0) * (v.refl(i + 1) + v.refl(i - 1))
          + T(1997.0 / 25920.0) * (v.refl(i + 2) + v.refl(i - 2))
          + T(149.0 / 12960.0) * (v.refl(i + 3) + v.refl(i - 3))
@@ -171,9 +176,10 @@ __device__ __forceinline__ T gauss_rhs(const LineView<T>& v, int i)
 
 // 5-point fourth difference at node i (one-sided near non-periodic ends: the nearest
 // complete stencil), the d^4/dxi^4 of Eq. 7
-template <typename T>
-__device__ __forceinline__ T d4_row(const LineView<T>& v, int i)
+template <typename V>
+__device__ __forceinline__ typename V::value_type d4_row(const V& v, int i)
 {
+    using T = typename V::value_type;
     int c = i;
     if (!v.per) c = c < 2 ? 2 : (c > v.N - 3 ? v.N - 3 : c);
     return v.at(c - 2) - T(4) * v.at(c - 1) + T(6) * v.at(c) - T(4) * v.at(c + 1) + v.at(c + 2);

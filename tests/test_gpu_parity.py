@@ -335,3 +335,34 @@ def test_fp64_jacobians_vs_fp32_coordinates(wd, oracle):
     print("metric error: FP32_METRIC64 %.2e, FP32 %.2e" % (err[1], err[2]))
     assert err[1] <= 1e-11
     assert err[2] > 100 * err[1] and err[2] <= 1e-2
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("gname,scheme,kw", [
+    ("cyl16x257x512", 4, dict(equation=1, curvature=1, alpha_f=0.495)),
+    ("ellipse129x256", 4, dict(equation=1)),
+    ("channel128x65", 4, dict(equation=0)),
+    ("square65", 1, dict(equation=0)),
+])
+def test_partition_passes_match_pcr_passes(wd, monkeypatch, prec, gname, scheme, kw):
+    """The fused 2-D step with the warp partition line solves (wd_part2d.cu) against the
+    same step with the PCR line solves (WD_PART_OFF=1): the same systems, only the
+    elimination order differs (FP64 to round-off, FP32 to a few ulps of the field)."""
+    mk = {"cyl16x257x512": lambda: W.stack([W.cylinder(257, 512, 1.03, r_wall=0.5 * (1 + 0.01 * k)) for k in range(4)]),
+          "ellipse129x256": lambda: W.ellipse(129, 256, 2.7),
+          "channel128x65": lambda: W.channel(128, 65),
+          "square65": lambda: W.square(65)}[gname]
+    spec = mk()
+    p = wd.default_params(scheme, **kw)
+    phi0 = W.random_field(spec, 4) * 0.05 + np.hypot(*spec.xyz[:2])
+    out = {}
+    for off in ("0", "1"):
+        monkeypatch.setenv("WD_PART_OFF", off)
+        g = wd.Grid(spec, prec, scheme)
+        r, _ = g.steps(p, g.as_field(phi0), 3, kind=0)
+        rp, _ = g.steps(p, g.as_field(phi0), 2, kind=1)
+        out[off] = (to_np(r), to_np(rp))
+        g.close()
+    tol = 1e-11 if prec == 0 else 2e-5
+    for a, b in zip(out["0"], out["1"]):
+        np.testing.assert_allclose(a, b, atol=tol * scale(b), rtol=0)
