@@ -21,16 +21,22 @@
 
 namespace wd {
 
-constexpr int P2_LPB = 8;                 // lines per block = warps per block
-constexpr int P2_THREADS = 32 * P2_LPB;
+// lines per block = warps per block (direction 1 stages 32-byte segments of 8 neighbouring
+// lines per row)
+constexpr int P2_LPB0 = 8, P2_LPB1 = 8;
+// resident blocks per SM asked of the compiler
+#define P2_MINB(T, LPB) (sizeof(T) == 8 ? 2 : 4)
+#define P2_MINB_DIV(T, LPB) (sizeof(T) == 8 ? 1 : 3)
 
 // padded line layout in shared memory: row i at i + i / 32 when R is even (so that the 32
-// lanes, R rows apart, fall in distinct banks), line stride odd
+// lanes, R rows apart, fall in distinct banks); the line stride is 4 modulo 32, so that the
+// 8 lines x 4 rows touched by a warp in the direction-1 staging order hit distinct banks
 template <int R>
 struct PLayout {
     static constexpr int NP = 32 * R;
     static constexpr int PAD = (R % 2 == 0);
-    static constexpr int LS = NP + (PAD ? R : 0) + 1;
+    static constexpr int USED = NP + (PAD ? R : 0);
+    static constexpr int LS = (USED + 27) / 32 * 32 + 4;
     __device__ static __forceinline__ int at(int i) { return PAD ? i + (i >> 5) : i; }
 };
 
@@ -52,69 +58,105 @@ struct PView {
     }
 };
 
-// Solves the line system for the right-hand sides held in x (rows lane*R + k); see
-// PartTab.  Every lane of the warp must call it.
-template <typename T, int R>
-__device__ __forceinline__ void part_solve(T (&x)[R], const PartTab<T>& tb, int lane)
+// Solves the line system for NF right-hand sides held in x[f] (rows lane*R + k); see
+// PartTab.  Each table value is loaded once for all NF fields.  Every lane of the warp must
+// call it.
+template <typename T, int R, int NF>
+__device__ __forceinline__ void part_solve(T (&x)[NF][R], const PartTab<T>& tb, int lane)
 {
     constexpr int m = R - 1;
     const T* __restrict__ loc = tb.loc;
     const T* __restrict__ sep = tb.sep;
-    x[0] *= __ldg(loc + (1 * m + 0) * 32 + lane);
+    {
+        const T iw = __ldg(loc + (1 * m + 0) * 32 + lane);
 #pragma unroll
-    for (int k = 1; k < m; k++)
-        x[k] = (x[k] - __ldg(loc + (0 * m + k) * 32 + lane) * x[k - 1]) * __ldg(loc + (1 * m + k) * 32 + lane);
+        for (int f = 0; f < NF; f++) x[f][0] *= iw;
+    }
 #pragma unroll
-    for (int k = m - 2; k >= 0; k--) x[k] -= __ldg(loc + (2 * m + k) * 32 + lane) * x[k + 1];
-    const T ynext = __shfl_sync(0xffffffffu, x[0], (lane + 1) & 31);
-    T d = x[R - 1] - __ldg(sep + 0 * 32 + lane) * x[m - 1] - __ldg(sep + 1 * 32 + lane) * ynext;
+    for (int k = 1; k < m; k++) {
+        const T la = __ldg(loc + (0 * m + k) * 32 + lane), iw = __ldg(loc + (1 * m + k) * 32 + lane);
+#pragma unroll
+        for (int f = 0; f < NF; f++) x[f][k] = (x[f][k] - la * x[f][k - 1]) * iw;
+    }
+#pragma unroll
+    for (int k = m - 2; k >= 0; k--) {
+        const T g = __ldg(loc + (2 * m + k) * 32 + lane);
+#pragma unroll
+        for (int f = 0; f < NF; f++) x[f][k] -= g * x[f][k + 1];
+    }
+    const T as = __ldg(sep + 0 * 32 + lane), cs = __ldg(sep + 1 * 32 + lane);
+    T d[NF];
+#pragma unroll
+    for (int f = 0; f < NF; f++) {
+        const T ynext = __shfl_sync(0xffffffffu, x[f][0], (lane + 1) & 31);
+        d[f] = x[f][R - 1] - as * x[f][m - 1] - cs * ynext;
+    }
 #pragma unroll
     for (int lev = 0; lev < 5; lev++) {
         const int h = 1 << lev;
-        const T dm = __shfl_sync(0xffffffffu, d, (lane - h) & 31);
-        const T dp = __shfl_sync(0xffffffffu, d, (lane + h) & 31);
-        d += __ldg(sep + (2 + lev) * 32 + lane) * dm + __ldg(sep + (7 + lev) * 32 + lane) * dp;
-    }
-    const T s = d * __ldg(sep + 12 * 32 + lane);
-    const T sp = __shfl_sync(0xffffffffu, s, (lane + 31) & 31);
+        const T al = __ldg(sep + (2 + lev) * 32 + lane), ga = __ldg(sep + (7 + lev) * 32 + lane);
 #pragma unroll
-    for (int k = 0; k < m; k++)
-        x[k] += __ldg(loc + (3 * m + k) * 32 + lane) * sp + __ldg(loc + (4 * m + k) * 32 + lane) * s;
-    x[R - 1] = s;
+        for (int f = 0; f < NF; f++) {
+            const T dm = __shfl_sync(0xffffffffu, d[f], (lane - h) & 31);
+            const T dp = __shfl_sync(0xffffffffu, d[f], (lane + h) & 31);
+            d[f] += al * dm + ga * dp;
+        }
+    }
+    const T ib = __ldg(sep + 12 * 32 + lane);
+    T s[NF], sp[NF];
+#pragma unroll
+    for (int f = 0; f < NF; f++) {
+        s[f] = d[f] * ib;
+        sp[f] = __shfl_sync(0xffffffffu, s[f], (lane + 31) & 31);
+    }
+#pragma unroll
+    for (int k = 0; k < m; k++) {
+        const T P = __ldg(loc + (3 * m + k) * 32 + lane), Q = __ldg(loc + (4 * m + k) * 32 + lane);
+#pragma unroll
+        for (int f = 0; f < NF; f++) x[f][k] += P * sp[f] + Q * s[f];
+    }
+#pragma unroll
+    for (int f = 0; f < NF; f++) x[f][R - 1] = s[f];
+}
+
+template <typename T, int R>
+__device__ __forceinline__ void part_solve(T (&x)[R], const PartTab<T>& tb, int lane)
+{
+    part_solve<T, R, 1>(reinterpret_cast<T(&)[1][R]>(x), tb, lane);
 }
 
 // visits the nodes (l, i) of the block's lines in an order whose global accesses are
 // coalesced; the same thread gets the same nodes in every call
-template <typename F>
+template <int LPB, typename F>
 __device__ __forceinline__ void p2_nodes(const Dims& D, int dir, int q0, int nl, F&& fn)
 {
     const int N = D.n[dir];
     if (dir == 0) {
         for (int l = 0; l < nl; l++) {
             const long long base = D.line_base(0, q0 + l);
-            for (int i = threadIdx.x; i < N; i += P2_THREADS) fn(l, i, base + i);
+            for (int i = threadIdx.x; i < N; i += 32 * LPB) fn(l, i, base + i);
         }
     } else {
-        const int l = threadIdx.x & (P2_LPB - 1);
+        const int l = threadIdx.x & (LPB - 1);
         if (l >= nl) return;
         const long long st = D.stride(dir);
         const long long base = D.line_base(dir, q0 + l);
-        for (int i = threadIdx.x / P2_LPB; i < N; i += P2_THREADS / P2_LPB) fn(l, i, base + (long long)i * st);
+        for (int i = threadIdx.x / LPB; i < N; i += 32) fn(l, i, base + (long long)i * st);
     }
 }
 
 // ---- A: derivative of phi along one direction (+ LAD fourth difference) -------------------
-template <typename T, typename M, int R>
-__global__ void __launch_bounds__(P2_THREADS) k_p2_deriv(F2Args<T, M> a, PartTab<T> tb, int dir)
+template <typename T, typename M, int R, int LPB>
+__global__ void __launch_bounds__(32 * LPB, P2_MINB(T, LPB)) k_p2_deriv(F2Args<T, M> a, PartTab<T> tb, int dir)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
     using Lay = PLayout<R>;
     T* Ph = reinterpret_cast<T*>(smraw);
-    T* Dv = Ph + P2_LPB * Lay::LS;
+    T* Dv = Ph + LPB * Lay::LS;
     const Dims& D = a.D;
     const int N = D.n[dir], per = D.per[dir];
-    const int q0 = blockIdx.x * P2_LPB, nl = min(P2_LPB, D.nlines(dir) - q0);
-    p2_nodes(D, dir, q0, nl, [&](int l, int i, long long e) { Ph[l * Lay::LS + Lay::at(i)] = a.src[e]; });
+    const int q0 = blockIdx.x * LPB, nl = min(LPB, D.nlines(dir) - q0);
+    p2_nodes<LPB>(D, dir, q0, nl, [&](int l, int i, long long e) { Ph[l * Lay::LS + Lay::at(i)] = a.src[e]; });
     __syncthreads();
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (w < nl) {
@@ -136,7 +178,7 @@ __global__ void __launch_bounds__(P2_THREADS) k_p2_deriv(F2Args<T, M> a, PartTab
     T* Dout = dir == 0 ? a.D0 : a.D1;
     T* Lout = dir == 0 ? a.L0 : a.L1;
     const long long tot = D.total;
-    p2_nodes(D, dir, q0, nl, [&](int l, int i, long long e) {
+    p2_nodes<LPB>(D, dir, q0, nl, [&](int l, int i, long long e) {
         Dout[e] = Dv[l * Lay::LS + Lay::at(i)];
         if (a.lad) {
             const PView<T, R> v{Ph + l * Lay::LS, N, per};
@@ -147,20 +189,20 @@ __global__ void __launch_bounds__(P2_THREADS) k_p2_deriv(F2Args<T, M> a, PartTab
 
 // ---- B: metric-weighted divergence parts along one direction ------------------------------
 // (direction 0 also smooths C|LAD| along its lines, the first half of the Gaussian)
-template <typename T, typename M, int NF, int R>
-__global__ void __launch_bounds__(P2_THREADS) k_p2_div(F2Args<T, M> a, PartTab<T> tb, int dir)
+template <typename T, typename M, int NF, int R, int LPB>
+__global__ void __launch_bounds__(32 * LPB, P2_MINB_DIV(T, LPB)) k_p2_div(F2Args<T, M> a, PartTab<T> tb, int dir)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
     using Lay = PLayout<R>;
-    constexpr int BUF = P2_LPB * Lay::LS;
+    constexpr int BUF = LPB * Lay::LS;
     T* U = reinterpret_cast<T*>(smraw);
     T* G = U + NF * BUF;
     const Dims& D = a.D;
     const int N = D.n[dir], per = D.per[dir];
-    const int q0 = blockIdx.x * P2_LPB, nl = min(P2_LPB, D.nlines(dir) - q0);
+    const int q0 = blockIdx.x * LPB, nl = min(LPB, D.nlines(dir) - q0);
     const long long tot = D.total;
     const bool gauss = dir == 0 && a.lad;
-    p2_nodes(D, dir, q0, nl, [&](int l, int i, long long e) {
+    p2_nodes<LPB>(D, dir, q0, nl, [&](int l, int i, long long e) {
         const int s = l * Lay::LS + Lay::at(i);
         const M d0 = M(a.D0[e]), d1 = M(a.D1[e]);
         const M ux = a.xi[0 * tot + e] * d0 + a.xi[3 * tot + e] * d1;   // xi_x D0 + eta_x D1
@@ -168,9 +210,9 @@ __global__ void __launch_bounds__(P2_THREADS) k_p2_div(F2Args<T, M> a, PartTab<T
         U[s] = T(ux);
         U[BUF + s] = T(uy);
         if (NF == 4) {
-            const M g = sqrt(ux * ux + uy * uy) + M(a.eps0);
-            U[2 * BUF + s] = T(ux / g);
-            U[3 * BUF + s] = T(uy / g);
+            const M ig = M(1) / (sqrt(ux * ux + uy * uy) + M(a.eps0));
+            U[2 * BUF + s] = T(ux * ig);
+            U[3 * BUF + s] = T(uy * ig);
         }
         if (gauss) {
             const T v = a.L0[e] + a.L1[e];
@@ -179,23 +221,32 @@ __global__ void __launch_bounds__(P2_THREADS) k_p2_div(F2Args<T, M> a, PartTab<T
     });
     __syncthreads();
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // fields solved together (one load of each table value for the group); one at a time
+    // keeps the registers low enough for two resident blocks
+    constexpr int GF = 1;
     if (w < nl) {
 #pragma unroll 1
-        for (int f = 0; f < NF; f++) {
-            T* F = U + f * BUF + w * Lay::LS;
-            const PView<T, R> v{F, N, per};
-            T x[R];
+        for (int f0 = 0; f0 < NF; f0 += GF) {
+            T x[GF][R];
 #pragma unroll
-            for (int k = 0; k < R; k++) {
-                const int i = lane * R + k;
-                x[k] = i < N ? deriv_rhs(v, i, a.scheme) : T(0);
+            for (int f = 0; f < GF; f++) {
+                const PView<T, R> v{U + (f0 + f) * BUF + w * Lay::LS, N, per};
+#pragma unroll
+                for (int k = 0; k < R; k++) {
+                    const int i = lane * R + k;
+                    x[f][k] = i < N ? deriv_rhs(v, i, a.scheme) : T(0);
+                }
             }
-            if (tb.implicit) part_solve<T, R>(x, tb, lane);
+            if (tb.implicit) part_solve<T, R, GF>(x, tb, lane);
             __syncwarp();
 #pragma unroll
-            for (int k = 0; k < R; k++) {
-                const int i = lane * R + k;
-                if (i < N) F[Lay::at(i)] = x[k];
+            for (int f = 0; f < GF; f++) {
+                T* F = U + (f0 + f) * BUF + w * Lay::LS;
+#pragma unroll
+                for (int k = 0; k < R; k++) {
+                    const int i = lane * R + k;
+                    if (i < N) F[Lay::at(i)] = x[f][k];
+                }
             }
             __syncwarp();
         }
@@ -203,7 +254,7 @@ __global__ void __launch_bounds__(P2_THREADS) k_p2_div(F2Args<T, M> a, PartTab<T
     __syncthreads();
     T* lap = dir == 0 ? a.LAP0 : a.LAP1;
     T* kap = dir == 0 ? a.KAP0 : a.KAP1;
-    p2_nodes(D, dir, q0, nl, [&](int l, int i, long long e) {
+    p2_nodes<LPB>(D, dir, q0, nl, [&](int l, int i, long long e) {
         const int s = l * Lay::LS + Lay::at(i);
         const M x0 = a.xi[(long long)(dir * 3 + 0) * tot + e];
         const M x1 = a.xi[(long long)(dir * 3 + 1) * tot + e];
@@ -215,26 +266,26 @@ __global__ void __launch_bounds__(P2_THREADS) k_p2_div(F2Args<T, M> a, PartTab<T
 
 // ---- F: filter along one direction; direction 1 with commit = 1 also applies the line
 // boundary conditions, reduces the change norms (Eq. 20) and commits the new state ------
-template <typename T, typename M, int R>
-__global__ void __launch_bounds__(P2_THREADS) k_p2_filter(F2Args<T, M> a, PartTab<T> tb, int dir, int commit)
+template <typename T, typename M, int R, int LPB>
+__global__ void __launch_bounds__(32 * LPB, P2_MINB(T, LPB)) k_p2_filter(F2Args<T, M> a, PartTab<T> tb, int dir, int commit)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
     __shared__ T cf[6][6];
-    __shared__ double s_ss[P2_LPB], s_mx[P2_LPB];
+    __shared__ double s_ss[LPB], s_mx[LPB];
     __shared__ int s_last;
     using Lay = PLayout<R>;
     T* A = reinterpret_cast<T*>(smraw);
     const Dims& D = a.D;
     const int N = D.n[dir], per = D.per[dir];
-    const int q0 = blockIdx.x * P2_LPB, nl = min(P2_LPB, D.nlines(dir) - q0);
+    const int q0 = blockIdx.x * LPB, nl = min(LPB, D.nlines(dir) - q0);
     const int tid = threadIdx.x;
-    for (int i = tid; i < 36; i += P2_THREADS) {
+    for (int i = tid; i < 36; i += 32 * LPB) {
         const int hw = i / 6, mm = i % 6;
         double v = 0.0;
         if (hw >= 1 && mm >= 1 && mm <= hw) v = 0.5 * a.fa[hw][mm] - (mm == 1 ? a.alpha_f : 0.0);
         cf[hw][mm] = T(v);
     }
-    p2_nodes(D, dir, q0, nl, [&](int l, int i, long long e) { A[l * Lay::LS + Lay::at(i)] = a.src[e]; });
+    p2_nodes<LPB>(D, dir, q0, nl, [&](int l, int i, long long e) { A[l * Lay::LS + Lay::at(i)] = a.src[e]; });
     __syncthreads();
     const int w = tid >> 5, lane = tid & 31;
     if (a.filter && w < nl) {
@@ -256,37 +307,41 @@ __global__ void __launch_bounds__(P2_THREADS) k_p2_filter(F2Args<T, M> a, PartTa
     }
     __syncthreads();
     if (!commit) {
-        p2_nodes(D, dir, q0, nl, [&](int l, int i, long long e) { a.dst[e] = A[l * Lay::LS + Lay::at(i)]; });
+        p2_nodes<LPB>(D, dir, q0, nl, [&](int l, int i, long long e) { a.dst[e] = A[l * Lay::LS + Lay::at(i)]; });
         return;
     }
-    // far-field / Neumann ends of the direction-1 lines (before the Dirichlet reset)
-    if (tid < nl) {
-        const int l = tid, qline = q0 + l;
-        const int line = (qline / D.n[0]) + D.n[2] * (qline % D.n[0]);   // face ratio index
-        T* F = A + l * Lay::LS;
-        for (int side = 0; side < 2; side++) {
+    // Epilogue: far-field / Neumann end nodes from the filtered values of their line (before
+    // the Dirichlet reset), Dirichlet nodes, commit, change norms.  A thread sums its own
+    // nodes' squared changes (at most R of them) in the state precision; the sums across
+    // threads and blocks are taken in double.
+    T ss_t = T(0), mx_t = T(0);
+    p2_nodes<LPB>(D, dir, q0, nl, [&](int l, int i, long long e) {
+        const T* F = A + l * Lay::LS;
+        T nv = F[Lay::at(i)];
+        if (i == 0 || i == N - 1) {
+            const int side = i == N - 1;
             int kind = side ? a.bchi1 : a.bclo1;
-            if (kind != WD_BC_FARFIELD && kind != WD_BC_NEUMANN) continue;
-            if (a.poisson) kind = WD_BC_NEUMANN;
-            const int b = side ? N - 1 : 0, s1 = side ? N - 2 : 1, s2 = side ? N - 3 : 2;
-            const T v1 = F[Lay::at(s1)], v2 = F[Lay::at(s2)];
-            if (kind == WD_BC_NEUMANN) F[Lay::at(b)] = v1;
-            else F[Lay::at(b)] = v1 + T((side ? a.ffr_hi : a.ffr_lo)[line]) * (v1 - v2);
+            if (kind == WD_BC_FARFIELD || kind == WD_BC_NEUMANN) {
+                if (a.poisson) kind = WD_BC_NEUMANN;
+                const T v1 = F[Lay::at(side ? N - 2 : 1)], v2 = F[Lay::at(side ? N - 3 : 2)];
+                if (kind == WD_BC_NEUMANN) nv = v1;
+                else {
+                    const int qline = q0 + l;
+                    const int line = (qline / D.n[0]) + D.n[2] * (qline % D.n[0]);   // face ratio index
+                    nv = v1 + T((side ? a.ffr_hi : a.ffr_lo)[line]) * (v1 - v2);
+                }
+            }
         }
-    }
-    __syncthreads();
-    double ss = 0.0, mx = 0.0;
-    p2_nodes(D, dir, q0, nl, [&](int l, int i, long long e) {
-        T nv = A[l * Lay::LS + Lay::at(i)];
         const bool dir_node = a.mask[e] != 0;
         if (dir_node) nv = a.poisson ? T(0) : a.dval[e];
         const T ov = a.phin[e];
         a.phin_w[e] = nv;
         if (dir_node) return;
-        const double d = double(nv) - double(ov);
-        ss += d * d;
-        mx = fmax(mx, fabs(d));
+        const T d = nv - ov;
+        ss_t += d * d;
+        mx_t = fmax(mx_t, fabs(d));
     });
+    double ss = double(ss_t), mx = double(mx_t);
     // block reduction, then the last block reduces the block partials in a fixed order
     for (int o = 16; o > 0; o >>= 1) {
         ss += __shfl_down_sync(0xffffffffu, ss, o);
@@ -299,7 +354,7 @@ __global__ void __launch_bounds__(P2_THREADS) k_p2_filter(F2Args<T, M> a, PartTa
     __syncthreads();
     if (tid == 0) {
         double t = 0.0, mm = 0.0;
-        for (int k = 0; k < P2_LPB; k++) {
+        for (int k = 0; k < LPB; k++) {
             t += s_ss[k];
             mm = fmax(mm, s_mx[k]);
         }
@@ -312,35 +367,25 @@ __global__ void __launch_bounds__(P2_THREADS) k_p2_filter(F2Args<T, M> a, PartTa
     __syncthreads();
     if (!s_last) return;
     __threadfence();
-    // blocks of stacked grid k are the contiguous range [k * bpm, (k + 1) * bpm)
+    // blocks of stacked grid k are the contiguous range [k * bpm, (k + 1) * bpm); warp w
+    // reduces grids w, w + LPB, ... in a fixed order
     const int bpm = gridDim.x / a.batch;
-    for (int k = 0; k < a.batch; k++) {
-        ss = 0.0;
-        mx = 0.0;
-        for (int b = k * bpm + tid; b < (k + 1) * bpm; b += P2_THREADS) {
-            ss += __ldcg(a.partial + 2 * b);
-            mx = fmax(mx, __ldcg(a.partial + 2 * b + 1));
+    for (int k = w; k < a.batch; k += LPB) {
+        double t = 0.0, mm = 0.0;
+        for (int b = k * bpm + lane; b < (k + 1) * bpm; b += 32) {
+            t += __ldcg(a.partial + 2 * b);
+            mm = fmax(mm, __ldcg(a.partial + 2 * b + 1));
         }
         for (int o = 16; o > 0; o >>= 1) {
-            ss += __shfl_down_sync(0xffffffffu, ss, o);
-            mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, o));
+            t += __shfl_down_sync(0xffffffffu, t, o);
+            mm = fmax(mm, __shfl_down_sync(0xffffffffu, mm, o));
         }
-        __syncthreads();
         if (lane == 0) {
-            s_ss[w] = ss;
-            s_mx[w] = mx;
-        }
-        __syncthreads();
-        if (tid == 0) {
-            double t = 0.0, mm = 0.0;
-            for (int q = 0; q < P2_LPB; q++) {
-                t += s_ss[q];
-                mm = fmax(mm, s_mx[q]);
-            }
             a.result[2 * k] = t;
             a.result[2 * k + 1] = mm;
         }
     }
+    __syncthreads();
     if (tid == 0) *a.counter = 0u;
 }
 
@@ -350,55 +395,63 @@ __global__ void __launch_bounds__(P2_THREADS) k_p2_filter(F2Args<T, M> a, PartTa
 
 static const size_t P2_SMEM_LIMIT = 200 * 1024;
 
-template <typename T, int R>
-static size_t p2_smem(int bufs)
+template <typename K>
+static void p2_allow(K kern)
 {
-    return (size_t)bufs * P2_LPB * PLayout<R>::LS * sizeof(T);
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P2_SMEM_LIMIT);
+}
+
+static size_t p2_ls(int R)
+{
+    const int used = 32 * R + (R % 2 == 0 ? R : 0);
+    return (size_t)((used + 27) / 32 * 32 + 4);
+}
+
+// shared-memory buffers (lines x LS) of each pass
+static int p2_bufs(int which, int dir, bool curv, bool lad)
+{
+    if (which == F2_DERIV) return 2;
+    if (which == F2_DIV) return (curv ? 4 : 2) + (dir == 0 && lad ? 1 : 0);
+    return 1;
+}
+
+template <typename T, typename M, int R, int LPB>
+static cudaError_t p2_launch_rl(const F2Args<T, M>& a, const PartTab<T>& tb, int which, int dir,
+                                cudaStream_t st)
+{
+    const Dims& D = a.D;
+    const int nb = (D.nlines(dir) + LPB - 1) / LPB;
+    const bool curv = a.curvature && !a.poisson;
+    const size_t sm = (size_t)p2_bufs(which, dir, curv, a.lad) * LPB * PLayout<R>::LS * sizeof(T);
+    if (sm > P2_SMEM_LIMIT) return cudaErrorNotSupported;
+    static bool attr = false;
+    if (!attr) {
+        p2_allow(k_p2_deriv<T, M, R, LPB>);
+        p2_allow(k_p2_div<T, M, 2, R, LPB>);
+        p2_allow(k_p2_div<T, M, 4, R, LPB>);
+        p2_allow(k_p2_filter<T, M, R, LPB>);
+        cudaGetLastError();
+        attr = true;
+    }
+    if (which == F2_DERIV) {
+        k_p2_deriv<T, M, R, LPB><<<nb, 32 * LPB, sm, st>>>(a, tb, dir);
+    } else if (which == F2_DIV) {
+        if (curv) k_p2_div<T, M, 4, R, LPB><<<nb, 32 * LPB, sm, st>>>(a, tb, dir);
+        else k_p2_div<T, M, 2, R, LPB><<<nb, 32 * LPB, sm, st>>>(a, tb, dir);
+    } else {
+        const int commit = which == F2_FILTER;
+        if (commit && (dir != 1 || D.n[0] % LPB || nb > a.max_partials)) return cudaErrorNotSupported;
+        k_p2_filter<T, M, R, LPB><<<nb, 32 * LPB, sm, st>>>(a, tb, dir, commit);
+    }
+    return cudaGetLastError();
 }
 
 template <typename T, typename M, int R>
 static cudaError_t p2_launch_r(const F2Args<T, M>& a, const PartTab<T>& tb, int which, int dir,
                                cudaStream_t st)
 {
-    const Dims& D = a.D;
-    const int nb = (D.nlines(dir) + P2_LPB - 1) / P2_LPB;
-    if (which == F2_DERIV) {
-        const size_t sm = p2_smem<T, R>(2);
-        if (sm > P2_SMEM_LIMIT) return cudaErrorNotSupported;
-        static bool attr = false;
-        if (!attr && cudaFuncSetAttribute(k_p2_deriv<T, M, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)P2_SMEM_LIMIT) == cudaSuccess)
-            attr = true;
-        k_p2_deriv<T, M, R><<<nb, P2_THREADS, sm, st>>>(a, tb, dir);
-    } else if (which == F2_DIV) {
-        const bool curv = a.curvature && !a.poisson;
-        const int bufs = (curv ? 4 : 2) + (dir == 0 && a.lad ? 1 : 0);
-        const size_t sm = p2_smem<T, R>(bufs);
-        if (sm > P2_SMEM_LIMIT) return cudaErrorNotSupported;
-        static bool attr2 = false, attr4 = false;
-        if (curv) {
-            if (!attr4 && cudaFuncSetAttribute(k_p2_div<T, M, 4, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               (int)P2_SMEM_LIMIT) == cudaSuccess)
-                attr4 = true;
-            k_p2_div<T, M, 4, R><<<nb, P2_THREADS, sm, st>>>(a, tb, dir);
-        } else {
-            if (!attr2 && cudaFuncSetAttribute(k_p2_div<T, M, 2, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               (int)P2_SMEM_LIMIT) == cudaSuccess)
-                attr2 = true;
-            k_p2_div<T, M, 2, R><<<nb, P2_THREADS, sm, st>>>(a, tb, dir);
-        }
-    } else {
-        const size_t sm = p2_smem<T, R>(1);
-        if (sm > P2_SMEM_LIMIT) return cudaErrorNotSupported;
-        const int commit = which == F2_FILTER;
-        if (commit && (dir != 1 || D.n[0] % P2_LPB || nb > a.max_partials)) return cudaErrorNotSupported;
-        static bool attr = false;
-        if (!attr && cudaFuncSetAttribute(k_p2_filter<T, M, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)P2_SMEM_LIMIT) == cudaSuccess)
-            attr = true;
-        k_p2_filter<T, M, R><<<nb, P2_THREADS, sm, st>>>(a, tb, dir, commit);
-    }
-    return cudaGetLastError();
+    return dir == 0 ? p2_launch_rl<T, M, R, P2_LPB0>(a, tb, which, dir, st)
+                    : p2_launch_rl<T, M, R, P2_LPB1>(a, tb, which, dir, st);
 }
 
 template <typename T, typename M>
@@ -418,19 +471,17 @@ cudaError_t p2_launch(const F2Args<T, M>& a, const PartTab<T>& tb, int which, in
     }
 }
 
-// whether the passes of which (F2_DERIV, F2_DIV, P2_FILTER0 or F2_FILTER) fit direction dir
+// whether the pass `which` (F2_DERIV, F2_DIV, P2_FILTER0 or F2_FILTER) fits direction dir
 template <typename T, typename M>
 bool p2_supported(const F2Args<T, M>& a, const PartTab<T>& tb, int which, int dir)
 {
     if (!tb.ok) return false;
-    int bufs = 1;
-    if (which == F2_DERIV) bufs = 2;
-    if (which == F2_DIV) bufs = 5;
-    const size_t ls = (size_t)32 * tb.R + (tb.R % 2 == 0 ? tb.R : 0) + 1;
-    if ((size_t)bufs * P2_LPB * ls * sizeof(T) > P2_SMEM_LIMIT) return false;
+    const int lpb = dir == 0 ? P2_LPB0 : P2_LPB1;
+    const int bufs = which == F2_DIV ? 5 : p2_bufs(which, dir, false, false);
+    if ((size_t)bufs * lpb * p2_ls(tb.R) * sizeof(T) > P2_SMEM_LIMIT) return false;
     if (which == F2_FILTER) {
-        const int nb = (a.D.nlines(dir) + P2_LPB - 1) / P2_LPB;
-        if (dir != 1 || a.D.n[0] % P2_LPB || nb > a.max_partials) return false;
+        const int nb = (a.D.nlines(dir) + lpb - 1) / lpb;
+        if (dir != 1 || a.D.n[0] % lpb || nb > a.max_partials) return false;
     }
     return true;
 }
