@@ -551,12 +551,17 @@ struct Solver {
         return true;
     }
 
+    // stage s reads stage_src(s) and writes stage_dst(s): distinct arrays, because the stage
+    // kernel of a far-field node re-evaluates its inner neighbours from the stage input
+    T* stage_src(int s) { return s == 0 ? W(W_PHIN) : (s % 2 ? W(W_PHIS) : W(W_T0)); }
+    T* stage_dst(int s) { return s % 2 ? W(W_T0) : W(W_PHIS); }
+
     wd_status step_part2d(F2Args<T, M>& a)
     {
         const PartTab<T> dt0 = g->dtab[0].template pview<T>(), dt1 = g->dtab[1].template pview<T>();
         for (int s = 0; s < 4; s++) {
-            a.src = s == 0 ? W(W_PHIN) : W(W_PHIS);
-            a.dst = W(W_PHIS);
+            a.src = stage_src(s);
+            a.dst = stage_dst(s);
             a.stage = s;
             {
                 ProfScope ps(g, WD_K_DERIV);
@@ -573,8 +578,8 @@ struct Solver {
                 CK(f2_launch<T, M>(a, F2_STAGE, st));
             }
         }
-        a.src = W(W_PHIS);
-        a.dst = W(W_PHIS);
+        a.src = stage_dst(3);
+        a.dst = stage_dst(3);
         if (p->filter) {
             ProfScope ps(g, WD_K_FILTER);
             CK(p2_launch<T, M>(a, g->ftab[0].template pview<T>(), P2_FILTER0, 0, st));
@@ -596,8 +601,8 @@ struct Solver {
         }
         if (part2d(a)) return step_part2d(a);
         for (int s = 0; s < 4; s++) {
-            a.src = s == 0 ? W(W_PHIN) : W(W_PHIS);
-            a.dst = W(W_PHIS);
+            a.src = stage_src(s);
+            a.dst = stage_dst(s);
             a.stage = s;
             {
                 ProfScope ps(g, WD_K_DERIV);
@@ -612,8 +617,8 @@ struct Solver {
                 CK(f2_launch<T, M>(a, F2_STAGE, st));
             }
         }
-        if (p->filter) ST(filter_dir(0, p->alpha_f, W(W_PHIS), W(W_PHIS)));
-        a.src = W(W_PHIS);
+        if (p->filter) ST(filter_dir(0, p->alpha_f, stage_dst(3), stage_dst(3)));
+        a.src = stage_dst(3);
         ProfScope ps(g, WD_K_NORM);
         CK(f2_launch<T, M>(a, F2_FILTER, st));
         return WD_OK;
@@ -638,12 +643,15 @@ struct Solver {
         std::memset(&a, 0, sizeof(a));
         a.D = D;
         a.scheme = g->desc.scheme;
+        double s1 = 0.0, s2 = 0.0;
         for (int l = 0; l < 3; l++) {
-            a.ih[l] = 1.0 / g->h[l];
-            a.slad[l] = std::pow(g->h[l], p->lad_exp - 4.0);
-            a.sig1 += 1.0 / g->h[l];
-            a.sig2 += 1.0 / (g->h[l] * g->h[l]);
+            a.ih[l] = T(1.0 / g->h[l]);
+            a.slad[l] = T(std::pow(g->h[l], p->lad_exp - 4.0));
+            s1 += 1.0 / g->h[l];
+            s2 += 1.0 / (g->h[l] * g->h[l]);
         }
+        a.sig1 = T(s1);
+        a.sig2 = T(s2);
         a.phin = W(W_PHIN);
         a.acc = W(W_ACC);
         a.dtv = W(W_DT);
@@ -655,9 +663,9 @@ struct Solver {
         a.G2 = W(W_N2);
         a.mask = g->mask;
         a.dval = (const T*)g->dval;
-        a.eps = p->eps;
-        a.cfl = p->cfl;
-        a.C_lad = p->C_lad;
+        a.eps = T(p->eps);
+        a.cfl = T(p->cfl);
+        a.C_lad = T(p->C_lad);
         a.equation = p->equation;
         a.lad = p->equation == WD_HJ_LAD && !poisson;
         a.poisson = poisson;
@@ -676,6 +684,49 @@ struct Solver {
             }
             ProfScope ps(g, WD_K_POINT);
             CK(c3_launch<T>(a, C3_S, st));
+        }
+        // filter along 0, 1 and 2 with the warp partition passes; the direction-2 pass also
+        // resets the Dirichlet nodes, reduces the change norms and commits
+        F2Args<T, M> f;
+        std::memset(&f, 0, sizeof(f));
+        f.D = D;
+        f.src = W(W_PHIS);
+        f.dst = W(W_PHIS);
+        f.phin = W(W_PHIN);
+        f.phin_w = W(W_PHIN);
+        f.mask = g->mask;
+        f.dval = (const T*)g->dval;
+        f.bclo1 = f.bchi1 = WD_BC_WALL;
+        f.poisson = poisson;
+        f.filter = p->filter;
+        f.alpha_f = p->alpha_f;
+        f.partial = g->partial;
+        f.counter = g->counter;
+        f.result = g->result;
+        f.max_partials = g->npartial;
+        f.batch = 1;
+        bool part = !g->part_off;
+        if (p->filter) {
+            LineOp op;
+            ST(op_filter(p->alpha_f, op));
+            std::memcpy(f.fa, op.fa, sizeof(f.fa));
+        }
+        for (int d = 0; d < 3 && part; d++) {
+            const PartTab<T> ft = g->ftab[d].template pview<T>();
+            if (p->filter ? !p2_supported(f, ft, d == 2 ? F2_FILTER : P2_FILTER0, d)
+                          : (d == 2 && !p2_supported(f, g->dtab[2].template pview<T>(), F2_FILTER, d)))
+                part = false;
+        }
+        if (part) {
+            if (p->filter) {
+                ProfScope ps(g, WD_K_FILTER);
+                for (int d = 0; d < 2; d++)
+                    CK(p2_launch<T, M>(f, g->ftab[d].template pview<T>(), P2_FILTER0, d, st));
+            }
+            ProfScope ps(g, WD_K_NORM);
+            const PartTab<T> t2 = p->filter ? g->ftab[2].template pview<T>() : g->dtab[2].template pview<T>();
+            CK(p2_launch<T, M>(f, t2, F2_FILTER, 2, st));
+            return WD_OK;
         }
         if (p->filter) {
             for (int d = 0; d < 3; d++) ST(filter_dir(d, p->alpha_f, W(W_PHIS), W(W_PHIS)));

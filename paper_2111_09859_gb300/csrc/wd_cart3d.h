@@ -11,9 +11,9 @@ template <typename T>
 struct C3Args {
     Dims D;
     int scheme;                  // WD_E2 / WD_E4 / WD_E6
-    double ih[3];                // 1 / h_l
-    double slad[3];              // LAD scales s_l = h_l^(exponent - 4) (Eq. 7, diagonal metrics)
-    double sig1, sig2;           // sum_l 1/h_l, sum_l 1/h_l^2
+    T ih[3];                     // 1 / h_l
+    T slad[3];                   // LAD scales s_l = h_l^(exponent - 4) (Eq. 7, diagonal metrics)
+    T sig1, sig2;                // sum_l 1/h_l, sum_l 1/h_l^2
     const T* src;                // phi of the stage
     T* dst;                      // stage output
     const T* phin;               // state at the start of the pseudo step
@@ -23,7 +23,7 @@ struct C3Args {
     T *L, *G1, *G2;              // C|LAD|, smoothed along 0, along 0 and 1
     const uint8_t* mask;
     const T* dval;
-    double eps, cfl, C_lad;
+    T eps, cfl, C_lad;
     int equation, lad, stage, poisson;
 };
 

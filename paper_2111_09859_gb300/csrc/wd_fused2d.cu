@@ -26,9 +26,9 @@ template <typename T, typename M>
 __device__ __forceinline__ void grad_at(const F2Args<T, M>& a, long long node, M& ux, M& uy)
 {
     const long long tot = a.D.total;
-    const M d0 = M(a.D0[node]), d1 = M(a.D1[node]);
-    ux = a.xi[0 * tot + node] * d0 + a.xi[3 * tot + node] * d1;   // xi_x D0 + eta_x D1
-    uy = a.xi[1 * tot + node] * d0 + a.xi[4 * tot + node] * d1;   // xi_y D0 + eta_y D1
+    const M d0 = M(__ldg(a.D0 + node)), d1 = M(__ldg(a.D1 + node));
+    ux = __ldg(a.xi + 0 * tot + node) * d0 + __ldg(a.xi + 3 * tot + node) * d1;   // xi_x D0 + eta_x D1
+    uy = __ldg(a.xi + 1 * tot + node) * d0 + __ldg(a.xi + 4 * tot + node) * d1;   // xi_y D0 + eta_y D1
 }
 
 // ---- A: derivatives of phi along both directions (+ LAD fourth differences) ---------------
@@ -194,7 +194,7 @@ __device__ __forceinline__ T f2_stage_value(const F2Args<T, M>& a, long long e, 
     const int N1 = D.n[1];
     const long long st = D.stride(1);
     T Rv, dtv, gam = T(0), v = T(0), gm = T(0);
-    const T lap = a.LAP0[e] + a.LAP1[e];
+    const T lap = __ldg(a.LAP0 + e) + __ldg(a.LAP1 + e);
     if (a.poisson) {
         Rv = T(1) + lap;                                                     // Eq. 19
     } else {
@@ -211,7 +211,7 @@ __device__ __forceinline__ T f2_stage_value(const F2Args<T, M>& a, long long e, 
             const T w[5] = {T(3565.0 / 10368.0), T(3091.0 / 12960.0), T(1997.0 / 25920.0),
                             T(149.0 / 12960.0), T(107.0 / 103680.0)};
             const long long e0 = e - (long long)j * st;
-            T gl = w[0] * a.G0[e];
+            T gl = w[0] * __ldg(a.G0 + e);
 #pragma unroll
             for (int m = 1; m <= 4; m++) {
                 int jp = j + m, jm = j - m;
@@ -222,14 +222,14 @@ __device__ __forceinline__ T f2_stage_value(const F2Args<T, M>& a, long long e, 
                     jp = jp > N1 - 1 ? 2 * (N1 - 1) - jp : jp;
                     jm = jm < 0 ? -jm : jm;
                 }
-                gl += w[m] * (a.G0[e0 + (long long)jp * st] + a.G0[e0 + (long long)jm * st]);
+                gl += w[m] * (__ldg(a.G0 + e0 + (long long)jp * st) + __ldg(a.G0 + e0 + (long long)jm * st));
             }
             const T g1 = T(a.eps) * php;
             gam = g1 < gl ? g1 : gl;
         }
         if (a.curvature) {                                                   // Eq. 25
             v = T(0.001) * (T(1) - gm) * (T(1) - gm);
-            T corr = gm * (a.KAP0[e] + a.KAP1[e]);
+            T corr = gm * (__ldg(a.KAP0 + e) + __ldg(a.KAP1 + e));
             corr = corr > T(0) ? corr : T(0);
             Rv = T(1) + (gam + v) * (lap - corr) - g2;
         } else {
@@ -237,16 +237,16 @@ __device__ __forceinline__ T f2_stage_value(const F2Args<T, M>& a, long long e, 
         }
     }
     if (a.stage == 0) {
-        if (a.poisson) dtv = T(a.cfl) / T(a.sig2[e]);
+        if (a.poisson) dtv = T(a.cfl) / T(__ldg(a.sig2 + e));
         else {
             const T am = gm > T(1) ? gm : T(1);
-            dtv = T(a.cfl) / (T(a.sig1[e]) * am + (gam + v) * T(a.sig2[e]));
+            dtv = T(a.cfl) / (T(__ldg(a.sig1 + e)) * am + (gam + v) * T(__ldg(a.sig2 + e)));
         }
         if (own) a.dtv[e] = dtv;
     } else {
         dtv = a.dtv[e];
     }
-    const T n = a.phin[e];
+    const T n = __ldg(a.phin + e);
     T out;
     if (a.stage == 0) {
         if (own) a.acc[e] = Rv * T(1.0 / 6.0);

@@ -23,10 +23,9 @@ namespace wd {
 
 // lines per block = warps per block (direction 1 stages 32-byte segments of 8 neighbouring
 // lines per row)
-constexpr int P2_LPB0 = 8, P2_LPB1 = 8;
 // resident blocks per SM asked of the compiler
-#define P2_MINB(T, LPB) (sizeof(T) == 8 ? 2 : 4)
-#define P2_MINB_DIV(T, LPB) (sizeof(T) == 8 ? 1 : 3)
+#define P2_MINB(T, LPB) ((LPB) >= 32 ? 1 : (sizeof(T) == 8 ? 2 : 4))
+#define P2_MINB_DIV(T, LPB) ((LPB) >= 32 ? 1 : (sizeof(T) == 8 ? 1 : 3))
 
 // padded line layout in shared memory: row i at i + i / 32 when R is even (so that the 32
 // lanes, R rows apart, fall in distinct banks); the line stride is 4 modulo 32, so that the
@@ -182,7 +181,7 @@ __global__ void __launch_bounds__(32 * LPB, P2_MINB(T, LPB)) k_p2_deriv(F2Args<T
         Dout[e] = Dv[l * Lay::LS + Lay::at(i)];
         if (a.lad) {
             const PView<T, R> v{Ph + l * Lay::LS, N, per};
-            Lout[e] = T(a.lads[(long long)dir * tot + e] * M(d4_row(v, i)));
+            Lout[e] = T(__ldg(a.lads + (long long)dir * tot + e) * M(d4_row(v, i)));
         }
     });
 }
@@ -205,8 +204,8 @@ __global__ void __launch_bounds__(32 * LPB, P2_MINB_DIV(T, LPB)) k_p2_div(F2Args
     p2_nodes<LPB>(D, dir, q0, nl, [&](int l, int i, long long e) {
         const int s = l * Lay::LS + Lay::at(i);
         const M d0 = M(a.D0[e]), d1 = M(a.D1[e]);
-        const M ux = a.xi[0 * tot + e] * d0 + a.xi[3 * tot + e] * d1;   // xi_x D0 + eta_x D1
-        const M uy = a.xi[1 * tot + e] * d0 + a.xi[4 * tot + e] * d1;   // xi_y D0 + eta_y D1
+        const M ux = __ldg(a.xi + 0 * tot + e) * d0 + __ldg(a.xi + 3 * tot + e) * d1;   // xi_x D0 + eta_x D1
+        const M uy = __ldg(a.xi + 1 * tot + e) * d0 + __ldg(a.xi + 4 * tot + e) * d1;   // xi_y D0 + eta_y D1
         U[s] = T(ux);
         U[BUF + s] = T(uy);
         if (NF == 4) {
@@ -256,8 +255,8 @@ __global__ void __launch_bounds__(32 * LPB, P2_MINB_DIV(T, LPB)) k_p2_div(F2Args
     T* kap = dir == 0 ? a.KAP0 : a.KAP1;
     p2_nodes<LPB>(D, dir, q0, nl, [&](int l, int i, long long e) {
         const int s = l * Lay::LS + Lay::at(i);
-        const M x0 = a.xi[(long long)(dir * 3 + 0) * tot + e];
-        const M x1 = a.xi[(long long)(dir * 3 + 1) * tot + e];
+        const M x0 = __ldg(a.xi + (long long)(dir * 3 + 0) * tot + e);
+        const M x1 = __ldg(a.xi + (long long)(dir * 3 + 1) * tot + e);
         lap[e] = T(x0 * M(U[s]) + x1 * M(U[BUF + s]));
         if (NF == 4) kap[e] = T(x0 * M(U[2 * BUF + s]) + x1 * M(U[3 * BUF + s]));
         if (gauss) a.G0[e] = gauss_rhs(PView<T, R>{G + l * Lay::LS, N, per}, i);
@@ -272,9 +271,10 @@ __global__ void __launch_bounds__(32 * LPB, P2_MINB(T, LPB)) k_p2_filter(F2Args<
     extern __shared__ __align__(16) unsigned char smraw[];
     __shared__ T cf[6][6];
     __shared__ double s_ss[LPB], s_mx[LPB];
-    __shared__ int s_last;
     using Lay = PLayout<R>;
     T* A = reinterpret_cast<T*>(smraw);
+    T* O = A + LPB * Lay::LS;                                   // commit: old state
+    uint8_t* MK = reinterpret_cast<uint8_t*>(O + LPB * Lay::LS);   // commit: Dirichlet flags
     const Dims& D = a.D;
     const int N = D.n[dir], per = D.per[dir];
     const int q0 = blockIdx.x * LPB, nl = min(LPB, D.nlines(dir) - q0);
@@ -285,7 +285,17 @@ __global__ void __launch_bounds__(32 * LPB, P2_MINB(T, LPB)) k_p2_filter(F2Args<
         if (hw >= 1 && mm >= 1 && mm <= hw) v = 0.5 * a.fa[hw][mm] - (mm == 1 ? a.alpha_f : 0.0);
         cf[hw][mm] = T(v);
     }
-    p2_nodes<LPB>(D, dir, q0, nl, [&](int l, int i, long long e) { A[l * Lay::LS + Lay::at(i)] = a.src[e]; });
+    // every global load of the pass happens here (the commit epilogue then only stores), so
+    // that the loads of a thread's nodes are in flight together
+    if (commit)
+        p2_nodes<LPB>(D, dir, q0, nl, [&](int l, int i, long long e) {
+            const int s = l * Lay::LS + Lay::at(i);
+            A[s] = a.src[e];
+            O[s] = a.phin[e];
+            MK[s] = a.mask[e];
+        });
+    else
+        p2_nodes<LPB>(D, dir, q0, nl, [&](int l, int i, long long e) { A[l * Lay::LS + Lay::at(i)] = a.src[e]; });
     __syncthreads();
     const int w = tid >> 5, lane = tid & 31;
     if (a.filter && w < nl) {
@@ -318,7 +328,7 @@ __global__ void __launch_bounds__(32 * LPB, P2_MINB(T, LPB)) k_p2_filter(F2Args<
     p2_nodes<LPB>(D, dir, q0, nl, [&](int l, int i, long long e) {
         const T* F = A + l * Lay::LS;
         T nv = F[Lay::at(i)];
-        if (i == 0 || i == N - 1) {
+        if ((i == 0 || i == N - 1) && D.ndim == 2) {
             const int side = i == N - 1;
             int kind = side ? a.bchi1 : a.bclo1;
             if (kind == WD_BC_FARFIELD || kind == WD_BC_NEUMANN) {
@@ -332,9 +342,10 @@ __global__ void __launch_bounds__(32 * LPB, P2_MINB(T, LPB)) k_p2_filter(F2Args<
                 }
             }
         }
-        const bool dir_node = a.mask[e] != 0;
-        if (dir_node) nv = a.poisson ? T(0) : a.dval[e];
-        const T ov = a.phin[e];
+        const int s = l * Lay::LS + Lay::at(i);
+        const bool dir_node = MK[s] != 0;
+        if (dir_node) nv = a.poisson ? T(0) : __ldg(a.dval + e);
+        const T ov = O[s];
         a.phin_w[e] = nv;
         if (dir_node) return;
         const T d = nv - ov;
@@ -360,33 +371,50 @@ __global__ void __launch_bounds__(32 * LPB, P2_MINB(T, LPB)) k_p2_filter(F2Args<
         }
         a.partial[2 * blockIdx.x] = t;
         a.partial[2 * blockIdx.x + 1] = mm;
-        __threadfence();
-        const unsigned v = atomicAdd(a.counter, 1u);
-        s_last = (v == gridDim.x - 1);
     }
-    __syncthreads();
-    if (!s_last) return;
-    __threadfence();
-    // blocks of stacked grid k are the contiguous range [k * bpm, (k + 1) * bpm); warp w
-    // reduces grids w, w + LPB, ... in a fixed order
-    const int bpm = gridDim.x / a.batch;
-    for (int k = w; k < a.batch; k += LPB) {
+}
+
+// Per-grid change norms from the block partials of the commit pass, in a fixed order: the
+// blocks of stacked grid k are the contiguous range [k * bpm, (k + 1) * bpm); a group of
+// tpm threads (a power of two, >= 32) reduces one grid at a time.
+__global__ void __launch_bounds__(1024) k_p2_reduce(const double* __restrict__ partial, int nblocks,
+                                                    int batch, double* result)
+{
+    __shared__ double s_ss[32], s_mx[32];
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    int tpm = 1024;
+    while (tpm > 32 && tpm * batch > 1024) tpm >>= 1;
+    const int ngroups = 1024 / tpm, grp = tid / tpm, gt = tid % tpm, wpg = tpm / 32;
+    const int bpm = nblocks / batch;
+    const int rounds = (batch + ngroups - 1) / ngroups;
+    for (int r = 0; r < rounds; r++) {
+        const int k = r * ngroups + grp;
         double t = 0.0, mm = 0.0;
-        for (int b = k * bpm + lane; b < (k + 1) * bpm; b += 32) {
-            t += __ldcg(a.partial + 2 * b);
-            mm = fmax(mm, __ldcg(a.partial + 2 * b + 1));
-        }
+        if (k < batch)
+            for (int b = k * bpm + gt; b < (k + 1) * bpm; b += tpm) {
+                t += partial[2 * b];
+                mm = fmax(mm, partial[2 * b + 1]);
+            }
         for (int o = 16; o > 0; o >>= 1) {
             t += __shfl_down_sync(0xffffffffu, t, o);
             mm = fmax(mm, __shfl_down_sync(0xffffffffu, mm, o));
         }
         if (lane == 0) {
-            a.result[2 * k] = t;
-            a.result[2 * k + 1] = mm;
+            s_ss[w] = t;
+            s_mx[w] = mm;
         }
+        __syncthreads();
+        if (gt == 0 && k < batch) {
+            double u = 0.0, v = 0.0;
+            for (int q = 0; q < wpg; q++) {
+                u += s_ss[grp * wpg + q];
+                v = fmax(v, s_mx[grp * wpg + q]);
+            }
+            result[2 * k] = u;
+            result[2 * k + 1] = v;
+        }
+        __syncthreads();
     }
-    __syncthreads();
-    if (tid == 0) *a.counter = 0u;
 }
 
 // ------------------------------------------------------------------------------------
@@ -412,6 +440,7 @@ static int p2_bufs(int which, int dir, bool curv, bool lad)
 {
     if (which == F2_DERIV) return 2;
     if (which == F2_DIV) return (curv ? 4 : 2) + (dir == 0 && lad ? 1 : 0);
+    if (which == F2_FILTER) return 3;   // field, old state, Dirichlet flags (rounded up)
     return 1;
 }
 
@@ -424,34 +453,66 @@ static cudaError_t p2_launch_rl(const F2Args<T, M>& a, const PartTab<T>& tb, int
     const bool curv = a.curvature && !a.poisson;
     const size_t sm = (size_t)p2_bufs(which, dir, curv, a.lad) * LPB * PLayout<R>::LS * sizeof(T);
     if (sm > P2_SMEM_LIMIT) return cudaErrorNotSupported;
-    static bool attr = false;
-    if (!attr) {
-        p2_allow(k_p2_deriv<T, M, R, LPB>);
-        p2_allow(k_p2_div<T, M, 2, R, LPB>);
-        p2_allow(k_p2_div<T, M, 4, R, LPB>);
-        p2_allow(k_p2_filter<T, M, R, LPB>);
-        cudaGetLastError();
-        attr = true;
-    }
     if (which == F2_DERIV) {
+        static bool attr = false;
+        if (!attr) p2_allow(k_p2_deriv<T, M, R, LPB>), attr = true;
         k_p2_deriv<T, M, R, LPB><<<nb, 32 * LPB, sm, st>>>(a, tb, dir);
     } else if (which == F2_DIV) {
+        static bool attr = false;
+        if (!attr) p2_allow(k_p2_div<T, M, 2, R, LPB>), p2_allow(k_p2_div<T, M, 4, R, LPB>), attr = true;
         if (curv) k_p2_div<T, M, 4, R, LPB><<<nb, 32 * LPB, sm, st>>>(a, tb, dir);
         else k_p2_div<T, M, 2, R, LPB><<<nb, 32 * LPB, sm, st>>>(a, tb, dir);
     } else {
+        static bool attr = false;
+        if (!attr) p2_allow(k_p2_filter<T, M, R, LPB>), attr = true;
         const int commit = which == F2_FILTER;
-        if (commit && (dir != 1 || D.n[0] % LPB || nb > a.max_partials)) return cudaErrorNotSupported;
+        if (commit && (nb > a.max_partials || (D.ndim == 2 && (dir != 1 || D.n[0] % LPB))))
+            return cudaErrorNotSupported;
         k_p2_filter<T, M, R, LPB><<<nb, 32 * LPB, sm, st>>>(a, tb, dir, commit);
+        if (commit) {
+            cudaError_t e = cudaGetLastError();
+            if (e != cudaSuccess) return e;
+            k_p2_reduce<<<1, 1024, 0, st>>>(a.partial, nb, a.batch, a.result);
+        }
     }
     return cudaGetLastError();
 }
+
+template <typename T, typename M, int R, int LPB>
+static cudaError_t p2_launch_rl_filter(const F2Args<T, M>& a, const PartTab<T>& tb, int which, int dir,
+                                       cudaStream_t st)
+{
+    const Dims& D = a.D;
+    const int nb = (D.nlines(dir) + LPB - 1) / LPB;
+    const int commit = which == F2_FILTER;
+    const size_t sm = (size_t)(commit ? 3 : 1) * LPB * PLayout<R>::LS * sizeof(T);
+    if (sm > P2_SMEM_LIMIT) return cudaErrorNotSupported;
+    static bool attr = false;
+    if (!attr) p2_allow(k_p2_filter<T, M, R, LPB>), attr = true;
+    if (commit && (nb > a.max_partials || D.ndim == 2)) return cudaErrorNotSupported;
+    k_p2_filter<T, M, R, LPB><<<nb, 32 * LPB, sm, st>>>(a, tb, dir, commit);
+    if (commit) {
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        k_p2_reduce<<<1, 1024, 0, st>>>(a.partial, nb, a.batch, a.result);
+    }
+    return cudaGetLastError();
+}
+
+// lines per block of a pass: 8 (whole rows for direction 0, 32-byte row segments of 8
+// neighbouring lines otherwise); the direction-2 filter of 3-D grids, whose rows lie a
+// whole plane apart, takes 32 lines for full 128-byte segments
+static int p2_lpb(int which, int dir) { return (dir == 2 && (which == F2_FILTER || which == P2_FILTER0)) ? 32 : 8; }
 
 template <typename T, typename M, int R>
 static cudaError_t p2_launch_r(const F2Args<T, M>& a, const PartTab<T>& tb, int which, int dir,
                                cudaStream_t st)
 {
-    return dir == 0 ? p2_launch_rl<T, M, R, P2_LPB0>(a, tb, which, dir, st)
-                    : p2_launch_rl<T, M, R, P2_LPB1>(a, tb, which, dir, st);
+    if (p2_lpb(which, dir) == 32) {
+        if (which == F2_DERIV || which == F2_DIV) return cudaErrorNotSupported;
+        return p2_launch_rl_filter<T, M, R, 32>(a, tb, which, dir, st);
+    }
+    return p2_launch_rl<T, M, R, 8>(a, tb, which, dir, st);
 }
 
 template <typename T, typename M>
@@ -476,12 +537,12 @@ template <typename T, typename M>
 bool p2_supported(const F2Args<T, M>& a, const PartTab<T>& tb, int which, int dir)
 {
     if (!tb.ok) return false;
-    const int lpb = dir == 0 ? P2_LPB0 : P2_LPB1;
+    const int lpb = p2_lpb(which, dir);
     const int bufs = which == F2_DIV ? 5 : p2_bufs(which, dir, false, false);
     if ((size_t)bufs * lpb * p2_ls(tb.R) * sizeof(T) > P2_SMEM_LIMIT) return false;
     if (which == F2_FILTER) {
         const int nb = (a.D.nlines(dir) + lpb - 1) / lpb;
-        if (dir != 1 || a.D.n[0] % lpb || nb > a.max_partials) return false;
+        if (nb > a.max_partials || (a.D.ndim == 2 && (dir != 1 || a.D.n[0] % lpb))) return false;
     }
     return true;
 }
