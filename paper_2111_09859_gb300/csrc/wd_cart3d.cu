@@ -18,80 +18,104 @@
 
 namespace wd {
 
-// Values f[t + o], o = -4 .. 4, of one grid line around node t (index e, stride st): the
-// offsets a formula may use are loaded, wrapped on periodic lines; on other lines offsets
-// outside the line are left 0 (no formula reads them).
-template <typename T>
-struct Win {
-    T v[9];
-    __device__ __forceinline__ T operator()(int o) const { return v[o + 4]; }
-};
+// Line helpers.  A node whose stencil stays inside its line (or any node of a periodic line
+// away from the wrap) loads its neighbours at constant offsets; the few nodes near a face
+// (or the wrap) evaluate the same formulas with computed indices straight from memory.
 
-template <int HW, typename T>
-__device__ __forceinline__ void load_win(Win<T>& w, const T* __restrict__ f, int e, int st, int t, int N,
-                                         int per)
+template <typename T>
+__device__ __forceinline__ T ld(const T* __restrict__ f, int e, int st, int t, int u, int N, int per)
 {
-    const bool inner = per ? (t >= HW && t < N - HW) : (t >= 4 && t < N - 4);
-    if (inner) {
-        const T* p = f + e;
-#pragma unroll
-        for (int o = -4; o <= 4; o++) w.v[o + 4] = (o >= -HW && o <= HW) ? __ldg(p + o * st) : T(0);
-        return;
-    }
-#pragma unroll
-    for (int o = -4; o <= 4; o++) {
-        int u = t + o;
-        if (per) u = u < 0 ? u + N : (u >= N ? u - N : u);
-        const bool ok = per ? (o >= -HW && o <= HW) : (u >= 0 && u < N);
-        w.v[o + 4] = ok ? __ldg(f + e + (u - t) * st) : T(0);
-    }
+    if (per) u = u < 0 ? u + N : (u >= N ? u - N : u);
+    return __ldg(f + e + (u - t) * st);
 }
 
-// explicit first derivative at line index t (Eq. 16 rows; the boundary rows of the line
-// passes: one-sided at the end node, centred 2nd order at the next, E4 at the third for E6)
+// first derivative of Eq. 16 at line index t with its boundary rows (one-sided at the end
+// node, centred 2nd order at the next, E4 at the third for E6); slow path
 template <int SCH, typename T>
-__device__ __forceinline__ T d1w(const Win<T>& w, int t, int N, int per)
+__device__ T d1_edge(const T* __restrict__ f, int e, int st, int t, int N, int per)
 {
-    constexpr int sch = SCH;
+#define LV(u) ld(f, e, st, t, (u), N, per)
     if (!per) {
-        if (t == 0) return (T(-25.0) * w(0) + T(48.0) * w(1) - T(36.0) * w(2) + T(16.0) * w(3) - T(3.0) * w(4)) * T(1.0 / 12.0);
-        if (t == N - 1) return -(T(-25.0) * w(0) + T(48.0) * w(-1) - T(36.0) * w(-2) + T(16.0) * w(-3) - T(3.0) * w(-4)) * T(1.0 / 12.0);
-        if (t == 1 || t == N - 2) return T(0.5) * (w(1) - w(-1));
+        if (t == 0) return (T(-25.0) * LV(0) + T(48.0) * LV(1) - T(36.0) * LV(2) + T(16.0) * LV(3) - T(3.0) * LV(4)) * T(1.0 / 12.0);
+        if (t == N - 1)
+            return -(T(-25.0) * LV(N - 1) + T(48.0) * LV(N - 2) - T(36.0) * LV(N - 3) + T(16.0) * LV(N - 4) - T(3.0) * LV(N - 5)) * T(1.0 / 12.0);
+        if (t == 1 || t == N - 2) return T(0.5) * (LV(t + 1) - LV(t - 1));
     }
-    const T a1 = w(1) - w(-1);
-    if (sch == WD_E2) return T(0.5) * a1;
-    const T a2 = w(2) - w(-2);
-    if (sch == WD_E4 || (!per && (t == 2 || t == N - 3))) return T(2.0 / 3.0) * a1 - T(1.0 / 12.0) * a2;
-    const T a3 = w(3) - w(-3);
+    const T a1 = LV(t + 1) - LV(t - 1);
+    if (SCH == WD_E2) return T(0.5) * a1;
+    const T a2 = LV(t + 2) - LV(t - 2);
+    if (SCH == WD_E4 || (!per && (t == 2 || t == N - 3))) return T(2.0 / 3.0) * a1 - T(1.0 / 12.0) * a2;
+    const T a3 = LV(t + 3) - LV(t - 3);
     return T(0.75) * a1 - T(0.15) * a2 + T(1.0 / 60.0) * a3;
 }
 
-// 5-point fourth difference (nearest complete stencil near non-periodic ends)
+// 5-point fourth difference, nearest complete stencil near non-periodic ends; slow path
 template <typename T>
-__device__ __forceinline__ T d4w(const Win<T>& w, int t, int N, int per)
+__device__ T d4_edge(const T* __restrict__ f, int e, int st, int t, int N, int per)
 {
-    int c = 0;
-    if (!per) c = (t < 2 ? 2 : (t > N - 3 ? N - 3 : t)) - t;
-    return w(c - 2) - T(4) * w(c - 1) + T(6) * w(c) - T(4) * w(c + 1) + w(c + 2);
+    int c = t;
+    if (!per) c = c < 2 ? 2 : (c > N - 3 ? N - 3 : c);
+    return LV(c - 2) - T(4) * LV(c - 1) + T(6) * LV(c) - T(4) * LV(c + 1) + LV(c + 2);
 }
 
-// truncated 9-point Gaussian (Kawai & Lele), even reflection at non-periodic ends
+// truncated 9-point Gaussian (Kawai & Lele), even reflection at non-periodic ends; slow path
 template <typename T>
-__device__ __forceinline__ T gaussw(const Win<T>& w, int t, int N, int per)
+__device__ T gauss_edge(const T* __restrict__ f, int e, int st, int t, int N, int per)
 {
     const T c[5] = {T(3565.0 / 10368.0), T(3091.0 / 12960.0), T(1997.0 / 25920.0), T(149.0 / 12960.0),
                     T(107.0 / 103680.0)};
-    T s = c[0] * w(0);
-#pragma unroll
+    T s = c[0] * LV(t);
     for (int m = 1; m <= 4; m++) {
-        int up = m, um = -m;
+        int up = t + m, um = t - m;
         if (!per) {
-            if (t + m > N - 1) up = 2 * (N - 1) - t - m - t;
-            if (t - m < 0) um = m - 2 * t;
+            up = up > N - 1 ? 2 * (N - 1) - up : up;
+            um = um < 0 ? -um : um;
         }
-        s += c[m] * (w(up) + w(um));
+        s += c[m] * (LV(up) + LV(um));
     }
     return s;
+#undef LV
+}
+
+// interior values f[t + o], |o| <= H, at constant offsets
+template <int H, typename T>
+__device__ __forceinline__ void win(T (&v)[2 * H + 1], const T* __restrict__ f, int e, int st)
+{
+    const T* p = f + e;
+#pragma unroll
+    for (int o = -H; o <= H; o++) v[o + H] = __ldg(p + o * st);
+}
+
+template <int SCH, int H, typename T>
+__device__ __forceinline__ T d1_in(const T (&v)[2 * H + 1])
+{
+    const T a1 = v[H + 1] - v[H - 1];
+    if (SCH == WD_E2) return T(0.5) * a1;
+    const T a2 = v[H + 2] - v[H - 2];
+    if (SCH == WD_E4) return T(2.0 / 3.0) * a1 - T(1.0 / 12.0) * a2;
+    const T a3 = v[H + 3] - v[H - 3];
+    return T(0.75) * a1 - T(0.15) * a2 + T(1.0 / 60.0) * a3;
+}
+
+template <int H, typename T>
+__device__ __forceinline__ T d4_in(const T (&v)[2 * H + 1])
+{
+    return v[H - 2] - T(4) * v[H - 1] + T(6) * v[H] - T(4) * v[H + 1] + v[H + 2];
+}
+
+template <typename T>
+__device__ __forceinline__ T gauss_in(const T (&v)[9])
+{
+    return T(3565.0 / 10368.0) * v[4] + T(3091.0 / 12960.0) * (v[5] + v[3]) + T(1997.0 / 25920.0) * (v[6] + v[2])
+         + T(149.0 / 12960.0) * (v[7] + v[1]) + T(107.0 / 103680.0) * (v[8] + v[0]);
+}
+
+// whether node t's stencil of half width H (and the one-sided rows, which reach 4) stays clear
+// of the ends of a non-periodic line, or of the wrap of a periodic one
+template <int H>
+__device__ __forceinline__ bool inner(int t, int N, int per)
+{
+    return per ? (t >= H && t < N - H) : (t >= 4 && t < N - 4);
 }
 
 struct C3Node {
@@ -127,14 +151,23 @@ __global__ void __launch_bounds__(256) k_c3_u(C3Args<T> a)
     if (!c3_node(a, q)) return;
     const Dims& D = a.D;
     constexpr int HD = C3Half<SCH>::HD;
-    constexpr int HW = LAD && HD < 2 ? 2 : HD;
+    constexpr int H = LAD && HD < 2 ? 2 : HD;
     T lad = T(0);
 #pragma unroll
     for (int l = 0; l < 3; l++) {
-        Win<T> w;
-        load_win<HW>(w, a.src, q.e, q.st[l], q.c[l], D.n[l], D.per[l]);
-        (l == 0 ? a.U0 : (l == 1 ? a.U1 : a.U2))[q.e] = d1w<SCH>(w, q.c[l], D.n[l], D.per[l]) * a.ih[l];
-        if (LAD) lad += d4w(w, q.c[l], D.n[l], D.per[l]) * a.slad[l];
+        const int t = q.c[l], N = D.n[l], per = D.per[l];
+        T d1, d4 = T(0);
+        if (inner<H>(t, N, per)) {
+            T v[2 * H + 1];
+            win<H>(v, a.src, q.e, q.st[l]);
+            d1 = d1_in<SCH, H>(v);
+            if (LAD) d4 = d4_in<H>(v);
+        } else {
+            d1 = d1_edge<SCH>(a.src, q.e, q.st[l], t, N, per);
+            if (LAD) d4 = d4_edge(a.src, q.e, q.st[l], t, N, per);
+        }
+        (l == 0 ? a.U0 : (l == 1 ? a.U1 : a.U2))[q.e] = d1 * a.ih[l];
+        if (LAD) lad += d4 * a.slad[l];
     }
     if (LAD) a.L[q.e] = a.C_lad * (lad < T(0) ? -lad : lad);
 }
@@ -145,9 +178,16 @@ __global__ void __launch_bounds__(256) k_c3_gauss(C3Args<T> a, int d, const T* _
     C3Node q;
     if (!c3_node(a, q)) return;
     const Dims& D = a.D;
-    Win<T> w;
-    load_win<4>(w, in, q.e, q.st[d], q.c[d], D.n[d], D.per[d]);
-    out[q.e] = gaussw(w, q.c[d], D.n[d], D.per[d]);
+    const int t = q.c[d], N = D.n[d], per = D.per[d];
+    T g;
+    if (inner<4>(t, N, per)) {
+        T v[9];
+        win<4>(v, in, q.e, q.st[d]);
+        g = gauss_in(v);
+    } else {
+        g = gauss_edge(in, q.e, q.st[d], t, N, per);
+    }
+    out[q.e] = g;
 }
 
 // EQ: 0 Poisson, 1 standard HJ, 2 LAD HJ, 3 eikonal (Gamma = 0)
@@ -162,24 +202,39 @@ __global__ void __launch_bounds__(256) k_c3_stage(C3Args<T> a)
     T lap = T(0);
 #pragma unroll
     for (int l = 0; l < 3; l++) {
-        Win<T> w;
-        load_win<HD>(w, l == 0 ? a.U0 : (l == 1 ? a.U1 : a.U2), e, q.st[l], q.c[l], D.n[l], D.per[l]);
-        lap += d1w<SCH>(w, q.c[l], D.n[l], D.per[l]) * a.ih[l];
+        const T* U = l == 0 ? a.U0 : (l == 1 ? a.U1 : a.U2);
+        const int t = q.c[l], N = D.n[l], per = D.per[l];
+        T d1;
+        if (inner<HD>(t, N, per)) {
+            T v[2 * HD + 1];
+            win<HD>(v, U, e, q.st[l]);
+            d1 = d1_in<SCH, HD>(v);
+        } else {
+            d1 = d1_edge<SCH>(U, e, q.st[l], t, N, per);
+        }
+        lap += d1 * a.ih[l];
     }
     T R, gam = T(0), gm = T(0);
     if (EQ == 0) {
         R = T(1) + lap;                                                  // Eq. 19
     } else {
-        const T ux = a.U0[e], uy = a.U1[e], uz = a.U2[e];
+        const T ux = __ldg(a.U0 + e), uy = __ldg(a.U1 + e), uz = __ldg(a.U2 + e);
         const T g2 = ux * ux + uy * uy + uz * uz;
         gm = sqrt(g2);
-        const T ph = a.src[e];
+        const T ph = a.src[e];   // also the stage output array (own node only)
         const T php = ph > T(0) ? ph : T(0);
         if (EQ == 1) gam = a.eps * php;                                  // Eq. 6
         else if (EQ == 2) {                                              // Eq. 7
-            Win<T> w;
-            load_win<4>(w, a.G2, e, q.st[2], q.c[2], D.n[2], D.per[2]);
-            const T g1 = a.eps * php, gl = gaussw(w, q.c[2], D.n[2], D.per[2]);
+            const int t = q.c[2], N = D.n[2], per = D.per[2];
+            T gl;
+            if (inner<4>(t, N, per)) {
+                T v[9];
+                win<4>(v, a.G2, e, q.st[2]);
+                gl = gauss_in(v);
+            } else {
+                gl = gauss_edge(a.G2, e, q.st[2], t, N, per);
+            }
+            const T g1 = a.eps * php;
             gam = g1 < gl ? g1 : gl;
         }
         R = T(1) + gam * lap - g2;                                       // Eqs. 5, 18
@@ -195,7 +250,7 @@ __global__ void __launch_bounds__(256) k_c3_stage(C3Args<T> a)
     } else {
         dtv = a.dtv[e];
     }
-    const T n = a.phin[e];
+    const T n = __ldg(a.phin + e);
     T out;
     if (a.stage == 0) {
         a.acc[e] = R * T(1.0 / 6.0);
@@ -209,7 +264,7 @@ __global__ void __launch_bounds__(256) k_c3_stage(C3Args<T> a)
     } else {
         out = n + dtv * (a.acc[e] + R * T(1.0 / 6.0));
     }
-    if (a.mask[e]) out = EQ == 0 ? T(0) : a.dval[e];
+    if (__ldg(a.mask + e)) out = EQ == 0 ? T(0) : __ldg(a.dval + e);
     a.dst[e] = out;
 }
 
