@@ -112,17 +112,28 @@ def peak_hbm():
         return 6800.0, "fallback"
 
 
-def algorithmic_bytes(cls, nodes, nd, es, ms, curv):
-    """Algorithmic DRAM bytes of one launch of a kernel class (the minimum each pass must
-    move): every field read once, every output written once."""
-    if cls == "deriv":          # phi -> d(phi)/dxi_l
-        return nodes * 2 * es
-    if cls == "div":            # U_m (and n_m) + nd metrics in, Laplacian (and kappa) r/w
-        nf = nd * (2 if curv else 1)
+def algorithmic_bytes(cls, nodes, nd, es, ms, curv, lad=True):
+    """Algorithmic DRAM bytes of one launch of a kernel class of the fused 2-D step (every
+    array a pass must touch read once, every output written once; one launch = one grid
+    direction for the line passes):
+      deriv  phi in, d(phi)/dxi_l out; LAD: s_l in, s_l d4_l(phi) out
+      div    D_0, D_1 and the 4 metrics of U in, the divergence part(s) out; the
+             direction-0 launch (half of them) also reads both LAD terms and writes their
+             smoothed sum
+      point  stage kernel: 13 state-size arrays in, the stage value and the RK4
+             accumulator out, plus the Dirichlet flags
+      filter / norm: the field in and out (norm: plus the old state and the flags)"""
+    if cls == "deriv":
+        return nodes * (2 * es + ((es + ms) if lad else 0))
+    if cls == "div":
         nout = 2 if curv else 1
-        return nodes * (nf * es + nd * ms + 2 * nout * es)
-    if cls in ("filter", "gauss"):
+        return int(nodes * (2 * es + 4 * ms + nout * es + (1.5 * es if lad else 0)))
+    if cls == "point":
+        return nodes * (15 * es + 1)
+    if cls == "filter":
         return nodes * 2 * es
+    if cls == "norm":
+        return nodes * (3 * es + 1)
     return None
 
 
@@ -241,7 +252,7 @@ def run_native(args, rank, world):
     e2e_value = cell_iters / (e2e_ms * 1e-3) / 1e6 if e2e_ms > 0 else None
 
     # roofline of the dominant kernel class
-    es, msz = 4, 8
+    es, msz = 4, 4      # FP32 state, metrics used in FP32 (computed in FP64)
     best = max((k for k in prof if prof[k][1] > 0), key=lambda k: prof[k][0])
     kms, kn = prof[best]
     ab = algorithmic_bytes(best, nodes, spec.ndim, es, msz, True)
@@ -259,11 +270,11 @@ def run_native(args, rank, world):
     out = {
         "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 3),
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32 (metrics f64)",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32 (metric Jacobians computed in f64)",
         "data": "synthetic",
         "config": {"workload": f"{BATCH} stacked cylinder O-grids 257x512 (r_wall 0.5(1+k/100), "
                                "r_out 10, ratio 1.03), C6 + LAD + curvature, alpha_f 0.495, "
-                               "FP32 state / FP64 metrics, tol RMS 1e-6 per cylinder, Poisson 100",
+                               "FP32 state and loop, metric Jacobians computed in FP64, tol RMS 1e-6 per cylinder, Poisson 100",
                    "batch": BATCH, "nodes": nodes, "pseudo_steps_per_solve": (iters + piters) / args.steps,
                    "l2_between_steps": "flushed (256 MB write)",
                    "parallelism": f"replicas x{world}"},
@@ -281,12 +292,148 @@ def run_native(args, rank, world):
                 "what": "wd_create_grid from host coordinates + wd_solve into pinned host memory + destroy"},
     }
     if rank == 0:
+        if not args.no_extras:
+            out["serving"] = serving_report(wd, args.full)
+            out["star_burn"] = star_report(wd, args.full)
+            d = duct_report(wd)
+            peak_hbm_gbs = peak_hbm()[0]
+            d["frac_of_fused_roofline"] = round(d["mcell_iter_s"] * 1e6 * 112 / (peak_hbm_gbs * 1e9), 4)
+            out["duct"] = d
         out["cpu_baseline"] = cpu_baseline()
         print(json.dumps(out), flush=True)
     if world > 1:
         import torch.distributed as dist
 
         dist.destroy_process_group()
+
+
+def serving_report(wd, full):
+    """Ellipse stream through the request loop (wd_server_*): the closed-loop saturation rate
+    of the request mix, then Poisson arrivals at 0.7 x that rate; p50 / p99 latency from
+    submission to completion, throughput.  Default: 12 requests (full: 1000)."""
+    import numpy as np
+    import torch
+
+    from paper_2111_09859_gb300 import workloads as W
+
+    n = 1000 if full else 12
+    shapes = W.ellipse_stream(n)
+    specs = [W.ellipse(*sh) for sh in shapes]
+    p = wd.default_params(wd.C6, equation=wd.HJ_LAD, tol_l2=1e-6, max_iters=20000)
+
+    def run(arrivals):
+        srv = wd.Server(max_active=32)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        tickets = []
+        for k, sp in enumerate(specs):
+            if arrivals is not None:
+                dt = arrivals[k] - (time.perf_counter() - t0)
+                if dt > 0:
+                    time.sleep(dt)
+            tickets.append((srv.submit(sp, p)[0], sp))
+        lat, cells = [], 0
+        for t, sp in tickets:
+            s_, st, l = srv.wait(t, 3600)
+            lat.append(l)
+            cells += sp.N * (st["iters"] + st["poisson_iters"])
+        span = time.perf_counter() - t0
+        info = srv.info()
+        srv.close()
+        return span, np.array(lat), cells, info
+
+    span, lat, cells, info = run(None)
+    rate_sat = n / span
+    rate = 0.7 * rate_sat
+    arr = W.poisson_arrivals(n, rate, seed=2111)
+    span2, lat2, cells2, info2 = run(arr)
+    return {"requests": n, "sizes": "ellipse O-grids 65x128 .. 1025x2048, AR U[1,4], seeds 9859 / 2111",
+            "precision": "FP32 (metrics computed in FP64), C6 + LAD, tol 1e-6",
+            "saturation_req_s": round(rate_sat, 3), "arrival_rate_req_s": round(rate, 3),
+            "p50_latency_s": round(float(np.percentile(lat2, 50)), 4),
+            "p99_latency_s": round(float(np.percentile(lat2, 99)), 4),
+            "throughput_req_s": round(n / span2, 3), "mcell_iter_s": round(cells2 / span2 / 1e6, 1),
+            "peak_concurrent": info2["peak_running"],
+            "closed_loop_p50_p99_s": [round(float(np.percentile(lat, 50)), 4), round(float(np.percentile(lat, 99)), 4)]}
+
+
+def star_report(wd, full):
+    """Receding star grain: 1025^2 box, E4 + LAD (Delta x^4 scale), eps 0.15, alpha_f 0.45,
+    FP32; the surface recedes by 0.002 per step, each step a warm re-solve on a session grid
+    through the request loop.  Default 50 steps (full: 200).  The burning perimeter of the
+    computed zero level against the marching-squares length of the exact offset field."""
+    import numpy as np
+    import torch
+
+    from paper_2111_09859_gb300 import workloads as W
+
+    steps = 200 if full else 50
+    sp = W.star(1025)
+    h, sd = sp.meta["h"], sp.meta["signed_distance"]
+    g = wd.Grid(sp, wd.FP32_METRIC64, wd.E4)
+    p = wd.default_params(wd.E4, equation=wd.HJ_LAD, eps=0.15, alpha_f=0.45, lad_exp=4.0, tol_l2=1e-7,
+                          max_iters=40000)
+    srv = wd.Server()
+    phi = g.empty()
+    t0 = time.perf_counter()
+    _, st0, lat0 = srv.wait(srv.submit_grid(g, p, phi), 3600)
+    lats, its = [], []
+    for k in range(1, steps + 1):
+        m, d = g.recede(phi, 0.002, -3 * h)
+        _, st, lat = srv.wait(srv.submit_grid(g, p, phi, warm=True, mask=m, dval=d), 3600)
+        lats.append(lat)
+        its.append(st["iters"])
+    torch.cuda.synchronize()
+    total = time.perf_counter() - t0
+    ex = sd - steps * 0.002
+    L = g.level_length(phi, 0.0)
+    Lx = g.level_length(g.as_field(ex), 0.0)
+    a = phi.double().cpu().numpy()
+    sel = (m.cpu().numpy() == 0) & (ex < 0.3)
+    err = float(np.abs(a - ex)[sel].max())
+    srv.close()
+    g.close()
+    return {"steps": steps, "grid": "1025x1025 on [-1,1]^2", "initial_solve_s": round(lat0, 4),
+            "initial_iters": st0["iters"], "step_p50_s": round(float(np.percentile(lats, 50)), 4),
+            "step_p99_s": round(float(np.percentile(lats, 99)), 4),
+            "warm_iters_median": int(np.median(its)), "total_s": round(total, 2),
+            "perimeter": round(L, 5), "perimeter_exact_field": round(Lx, 5),
+            "perimeter_rel_err": round((L - Lx) / Lx, 5), "max_err_near_port_h": round(err / h, 3)}
+
+
+def duct_report(wd):
+    """Square duct 256^3, E6 + LAD, FP32: Mcell-iter/s of the pseudo steps and the solve."""
+    import numpy as np
+    import torch
+
+    from paper_2111_09859_gb300 import workloads as W
+
+    sp = W.duct(256)
+    g = wd.Grid(sp, wd.FP32_METRIC64, wd.E6)
+    p = wd.default_params(wd.E6, equation=wd.HJ_LAD, tol_l2=1e-6, max_iters=5000)
+    x, y, z = sp.xyz
+    ex = np.minimum.reduce([y, 1 - y, z, 1 - z])
+    phi = g.as_field(ex)
+    g.steps(p, phi, 3)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record()
+    g.steps(p, phi, 20)
+    ev1.record()
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / 20
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    out, st = g.solve(p)
+    torch.cuda.synchronize()
+    ts = time.perf_counter() - t0
+    err = float(np.abs(out.double().cpu().numpy() - ex).max())
+    g.close()
+    return {"nodes": sp.N, "ms_per_pseudo_step": round(ms, 3), "mcell_iter_s": round(sp.N / (ms * 1e-3) / 1e6, 1),
+            "fused_min_bytes_per_cell_iter": 112,
+            "frac_of_fused_roofline": None,
+            "solve_s": round(ts, 3), "solve_iters": st["iters"] + st["poisson_iters"],
+            "max_err_vs_exact": err}
 
 
 def cpu_baseline(n_steps=12):
@@ -347,6 +494,8 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--full", action="store_true", help="serving: 1000 requests; star: 200 steps")
+    ap.add_argument("--no-extras", action="store_true", help="only the headline cylinder workload")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
