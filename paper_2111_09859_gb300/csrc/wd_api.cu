@@ -625,15 +625,25 @@ struct Solver {
     }
 
     // uniform Cartesian 3-D grids with an explicit scheme and walls / periodic faces only
+    // uniform Cartesian grids with an explicit scheme: 3-D with walls / periodic faces, or
+    // single 2-D grids of any faces (far-field / Neumann faces are applied after each stage)
     bool cart3d() const
     {
-        if (D.ndim != 3 || !g->cart || g->force_generic) return false;
+        if (!g->cart || g->force_generic || g->batch != 1) return false;
         const int sch = g->desc.scheme;
         if (sch == WD_C4 || sch == WD_C6) return false;
+        if (D.ndim == 2) return true;
         for (int d = 0; d < 3; d++)
             for (int k : {g->desc.bc_lo[d], g->desc.bc_hi[d]})
                 if (k == WD_BC_FARFIELD || k == WD_BC_NEUMANN) return false;
         return true;
+    }
+    bool faces_need_bc() const
+    {
+        for (int d = 0; d < D.ndim; d++)
+            for (int k : {g->desc.bc_lo[d], g->desc.bc_hi[d]})
+                if (k == WD_BC_FARFIELD || k == WD_BC_NEUMANN) return true;
+        return false;
     }
 
     wd_status step_cart3d(bool poisson)
@@ -644,7 +654,7 @@ struct Solver {
         a.D = D;
         a.scheme = g->desc.scheme;
         double s1 = 0.0, s2 = 0.0;
-        for (int l = 0; l < 3; l++) {
+        for (int l = 0; l < D.ndim; l++) {
             a.ih[l] = T(1.0 / g->h[l]);
             a.slad[l] = T(std::pow(g->h[l], p->lad_exp - 4.0));
             s1 += 1.0 / g->h[l];
@@ -680,10 +690,13 @@ struct Solver {
             if (a.lad) {
                 ProfScope ps(g, WD_K_GAUSS);
                 CK(c3_launch<T>(a, C3_GX, st));
-                CK(c3_launch<T>(a, C3_GY, st));
+                if (D.ndim == 3) CK(c3_launch<T>(a, C3_GY, st));
             }
-            ProfScope ps(g, WD_K_POINT);
-            CK(c3_launch<T>(a, C3_S, st));
+            {
+                ProfScope ps(g, WD_K_POINT);
+                CK(c3_launch<T>(a, C3_S, st));
+            }
+            if (faces_need_bc()) ST(bc(W(W_PHIS), poisson));
         }
         // filter along 0, 1 and 2 with the warp partition passes; the direction-2 pass also
         // resets the Dirichlet nodes, reduces the change norms and commits
@@ -705,7 +718,7 @@ struct Solver {
         f.result = g->result;
         f.max_partials = g->npartial;
         f.batch = 1;
-        bool part = !g->part_off;
+        bool part = !g->part_off && D.ndim == 3;
         if (p->filter) {
             LineOp op;
             ST(op_filter(p->alpha_f, op));
@@ -729,7 +742,15 @@ struct Solver {
             return WD_OK;
         }
         if (p->filter) {
-            for (int d = 0; d < 3; d++) ST(filter_dir(d, p->alpha_f, W(W_PHIS), W(W_PHIS)));
+            for (int d = 0; d < D.ndim; d++) {
+                const PartTab<T> ft = g->ftab[d].template pview<T>();
+                if (!g->part_off && p2_supported(f, ft, P2_FILTER0, d)) {
+                    ProfScope ps(g, WD_K_FILTER);
+                    CK(p2_launch<T, M>(f, ft, P2_FILTER0, d, st));
+                } else {
+                    ST(filter_dir(d, p->alpha_f, W(W_PHIS), W(W_PHIS)));
+                }
+            }
             ST(bc(W(W_PHIS), poisson));
         }
         ProfScope ps(g, WD_K_NORM);
@@ -1134,14 +1155,18 @@ static wd_status geometry_impl(wd_grid g, const double* xyz_host, const uint8_t*
         CK(cudaMemcpy2DAsync(g->xyz + m * tot, (size_t)D.pitch * 8,
                              xyz_host + (size_t)m * D.n[0] * D.n[1] * D.n[2], (size_t)D.n[0] * 8,
                              (size_t)D.n[0] * 8, (size_t)D.n[1] * D.n[2], cudaMemcpyHostToDevice, st));
-    // uniform Cartesian 3-D grid?  x = x0 + i hx, y = y0 + j hy, z = z0 + k hz at every node
+    // uniform Cartesian grid?  x = x0 + i hx, y = y0 + j hy (, z = z0 + k hz) at every node
     g->cart = 0;
-    if (D.ndim == 3) {
+    if (D.ndim == 3 || g->batch == 1) {
+        const bool d3 = D.ndim == 3;
         const size_t N = (size_t)D.n[0] * D.n[1] * D.n[2];
         const double* X = xyz_host;
-        const double *Y = xyz_host + N, *Z = xyz_host + 2 * N;
+        const double* Y = xyz_host + N;
         const size_t s1 = D.n[0], s2 = (size_t)D.n[0] * D.n[1];
-        double hx = X[1] - X[0], hy = Y[s1] - Y[0], hz = Z[s2] - Z[0];
+        std::vector<double> zero;
+        if (!d3) zero.assign(N, 0.0);
+        const double* Z = d3 ? xyz_host + 2 * N : zero.data();
+        double hx = X[1] - X[0], hy = Y[s1] - Y[0], hz = d3 ? Z[s2] - Z[0] : 1.0;
         bool ok = hx > 0 && hy > 0 && hz > 0;
         const double tx = 1e-9 * (std::fabs(X[0]) + D.n[0] * hx), ty = 1e-9 * (std::fabs(Y[0]) + D.n[1] * hy),
                      tz = 1e-9 * (std::fabs(Z[0]) + D.n[2] * hz);
@@ -1150,7 +1175,7 @@ static wd_status geometry_impl(wd_grid g, const double* xyz_host, const uint8_t*
                 for (int i = 0; i < D.n[0]; i++) {
                     const size_t q = i + s1 * j + s2 * k;
                     if (std::fabs(X[q] - (X[0] + i * hx)) > tx || std::fabs(Y[q] - (Y[0] + j * hy)) > ty ||
-                        std::fabs(Z[q] - (Z[0] + k * hz)) > tz) {
+                        (d3 && std::fabs(Z[q] - (Z[0] + k * hz)) > tz)) {
                         ok = false;
                         break;
                     }

@@ -1,9 +1,9 @@
-// wd_cart3d.cu -- pseudo-step kernels for uniform Cartesian 3-D grids with explicit schemes
-// (E2 / E4 / E6).  The metrics are then the constants d(xi_l)/d(x_m) = delta_lm / h_l, so
+// wd_cart3d.cu -- pseudo-step kernels for uniform Cartesian grids (3-D, and single 2-D grids
+// whose faces rule out the fused 2-D path) with explicit schemes (E2 / E4 / E6).  The metrics are then the constants d(xi_l)/d(x_m) = delta_lm / h_l, so
 //     U_l = D_l(phi) / h_l,   lap(phi) = sum_l D_l(U_l) / h_l   (Eq. 9 with diagonal metrics),
 //     LAD term (Eq. 7) = C | sum_l d4_l(phi) s_l |   (s_l = h_l^(exponent - 4)),
 // and every pass is a stencil along grid lines read straight from global memory (L1/L2 serve
-// the neighbours).  One RK stage = four launches:
+// the neighbours).  One RK stage = four launches in 3-D (three in 2-D, without GY):
 //   U   U_0, U_1, U_2 and the raw LAD term,
 //   GX  Gaussian of the LAD term along direction 0,
 //   GY  Gaussian along direction 1,
@@ -144,7 +144,7 @@ struct C3Half {
     static constexpr int HD = SCH == WD_E6 ? 3 : (SCH == WD_E4 ? 2 : 1);   // derivative
 };
 
-template <typename T, int SCH, int LAD>
+template <typename T, int ND, int SCH, int LAD>
 __global__ void __launch_bounds__(256) k_c3_u(C3Args<T> a)
 {
     C3Node q;
@@ -154,7 +154,7 @@ __global__ void __launch_bounds__(256) k_c3_u(C3Args<T> a)
     constexpr int H = LAD && HD < 2 ? 2 : HD;
     T lad = T(0);
 #pragma unroll
-    for (int l = 0; l < 3; l++) {
+    for (int l = 0; l < ND; l++) {
         const int t = q.c[l], N = D.n[l], per = D.per[l];
         T d1, d4 = T(0);
         if (inner<H>(t, N, per)) {
@@ -191,7 +191,7 @@ __global__ void __launch_bounds__(256) k_c3_gauss(C3Args<T> a, int d, const T* _
 }
 
 // EQ: 0 Poisson, 1 standard HJ, 2 LAD HJ, 3 eikonal (Gamma = 0)
-template <typename T, int SCH, int EQ>
+template <typename T, int ND, int SCH, int EQ>
 __global__ void __launch_bounds__(256) k_c3_stage(C3Args<T> a)
 {
     C3Node q;
@@ -201,7 +201,7 @@ __global__ void __launch_bounds__(256) k_c3_stage(C3Args<T> a)
     constexpr int HD = C3Half<SCH>::HD;
     T lap = T(0);
 #pragma unroll
-    for (int l = 0; l < 3; l++) {
+    for (int l = 0; l < ND; l++) {
         const T* U = l == 0 ? a.U0 : (l == 1 ? a.U1 : a.U2);
         const int t = q.c[l], N = D.n[l], per = D.per[l];
         T d1;
@@ -218,21 +218,24 @@ __global__ void __launch_bounds__(256) k_c3_stage(C3Args<T> a)
     if (EQ == 0) {
         R = T(1) + lap;                                                  // Eq. 19
     } else {
-        const T ux = __ldg(a.U0 + e), uy = __ldg(a.U1 + e), uz = __ldg(a.U2 + e);
+        const T ux = __ldg(a.U0 + e), uy = __ldg(a.U1 + e), uz = ND == 3 ? __ldg(a.U2 + e) : T(0);
         const T g2 = ux * ux + uy * uy + uz * uz;
         gm = sqrt(g2);
         const T ph = a.src[e];   // also the stage output array (own node only)
         const T php = ph > T(0) ? ph : T(0);
         if (EQ == 1) gam = a.eps * php;                                  // Eq. 6
         else if (EQ == 2) {                                              // Eq. 7
-            const int t = q.c[2], N = D.n[2], per = D.per[2];
+            // the last direction's half of the separable Gaussian
+            constexpr int L = ND - 1;
+            const T* G = ND == 3 ? a.G2 : a.G1;
+            const int t = q.c[L], N = D.n[L], per = D.per[L];
             T gl;
             if (inner<4>(t, N, per)) {
                 T v[9];
-                win<4>(v, a.G2, e, q.st[2]);
+                win<4>(v, G, e, q.st[L]);
                 gl = gauss_in(v);
             } else {
-                gl = gauss_edge(a.G2, e, q.st[2], t, N, per);
+                gl = gauss_edge(G, e, q.st[L], t, N, per);
             }
             const T g1 = a.eps * php;
             gam = g1 < gl ? g1 : gl;
@@ -268,18 +271,26 @@ __global__ void __launch_bounds__(256) k_c3_stage(C3Args<T> a)
     a.dst[e] = out;
 }
 
-template <typename T, int SCH>
+template <typename T, int ND, int SCH>
 static void c3_launch_s(const C3Args<T>& a, int which, dim3 grd, dim3 blk, cudaStream_t st)
 {
     if (which == C3_U) {
-        if (a.lad) k_c3_u<T, SCH, 1><<<grd, blk, 0, st>>>(a);
-        else k_c3_u<T, SCH, 0><<<grd, blk, 0, st>>>(a);
+        if (a.lad) k_c3_u<T, ND, SCH, 1><<<grd, blk, 0, st>>>(a);
+        else k_c3_u<T, ND, SCH, 0><<<grd, blk, 0, st>>>(a);
     } else {
-        if (a.poisson) k_c3_stage<T, SCH, 0><<<grd, blk, 0, st>>>(a);
-        else if (a.equation == WD_HJ_LAD) k_c3_stage<T, SCH, 2><<<grd, blk, 0, st>>>(a);
-        else if (a.equation == WD_HJ_STD) k_c3_stage<T, SCH, 1><<<grd, blk, 0, st>>>(a);
-        else k_c3_stage<T, SCH, 3><<<grd, blk, 0, st>>>(a);
+        if (a.poisson) k_c3_stage<T, ND, SCH, 0><<<grd, blk, 0, st>>>(a);
+        else if (a.equation == WD_HJ_LAD) k_c3_stage<T, ND, SCH, 2><<<grd, blk, 0, st>>>(a);
+        else if (a.equation == WD_HJ_STD) k_c3_stage<T, ND, SCH, 1><<<grd, blk, 0, st>>>(a);
+        else k_c3_stage<T, ND, SCH, 3><<<grd, blk, 0, st>>>(a);
     }
+}
+
+template <typename T, int ND>
+static void c3_launch_nd(const C3Args<T>& a, int which, dim3 grd, dim3 blk, cudaStream_t st)
+{
+    if (a.scheme == WD_E6) c3_launch_s<T, ND, WD_E6>(a, which, grd, blk, st);
+    else if (a.scheme == WD_E4) c3_launch_s<T, ND, WD_E4>(a, which, grd, blk, st);
+    else c3_launch_s<T, ND, WD_E2>(a, which, grd, blk, st);
 }
 
 template <typename T>
@@ -289,9 +300,8 @@ cudaError_t c3_launch(const C3Args<T>& a, int which, cudaStream_t st)
     const dim3 grd((a.D.n[0] + 31) / 32, (a.D.n[1] + 7) / 8, a.D.n[2]);
     if (which == C3_GX) k_c3_gauss<T><<<grd, blk, 0, st>>>(a, 0, a.L, a.G1);
     else if (which == C3_GY) k_c3_gauss<T><<<grd, blk, 0, st>>>(a, 1, a.G1, a.G2);
-    else if (a.scheme == WD_E6) c3_launch_s<T, WD_E6>(a, which, grd, blk, st);
-    else if (a.scheme == WD_E4) c3_launch_s<T, WD_E4>(a, which, grd, blk, st);
-    else c3_launch_s<T, WD_E2>(a, which, grd, blk, st);
+    else if (a.D.ndim == 3) c3_launch_nd<T, 3>(a, which, grd, blk, st);
+    else c3_launch_nd<T, 2>(a, which, grd, blk, st);
     return cudaGetLastError();
 }
 

@@ -366,3 +366,25 @@ def test_partition_passes_match_pcr_passes(wd, monkeypatch, prec, gname, scheme,
     tol = 1e-11 if prec == 0 else 2e-5
     for a, b in zip(out["0"], out["1"]):
         np.testing.assert_allclose(a, b, atol=tol * scale(b), rtol=0)
+
+
+@pytest.mark.parametrize("generic", [False, True])
+@pytest.mark.parametrize("eq", [0, 1])
+def test_cartesian_2d_steps_with_neumann_faces(wd, oracle, generic, eq, monkeypatch):
+    """Single uniform 2-D grids whose faces rule out the fused path (the star port with
+    zero-gradient box edges and an immersed Dirichlet port) take the Cartesian stencil path
+    unless WD_FORCE_GENERIC=1; both agree with the oracle over HJ and Poisson steps."""
+    if generic:
+        monkeypatch.setenv("WD_FORCE_GENERIC", "1")
+    spec = W.star(97)
+    prm = base_params(1, equation=eq, lad_exp=4.0, eps=0.15)
+    og = oracle_grid(oracle, spec, 1)
+    g = wd.Grid(spec, 0, 1)
+    phi0 = og.apply_bc(np.where(spec.mask == 1, spec.dval, spec.meta["signed_distance"])
+                       + 0.01 * W.random_field(spec, 5))
+    ref, _ = og.hj_steps(phi0, 4, **oracle_kw(1, prm))
+    out, _ = g.steps(gpu_params(wd, 1, prm), g.as_field(phi0), 4, kind=0)
+    np.testing.assert_allclose(to_np(out), ref, atol=1e-10 * scale(ref), rtol=0)
+    refp, _ = og.poisson_steps(np.zeros(spec.N), 10, **oracle_kw(1, prm))
+    outp, _ = g.steps(gpu_params(wd, 1, prm), g.as_field(np.zeros(spec.N)), 10, kind=1)
+    np.testing.assert_allclose(to_np(outp), refp, atol=1e-10 * scale(refp), rtol=0)
