@@ -1,4 +1,5 @@
-// wd_part2d.cu -- line passes of the fused 2-D pseudo step with the warp partition solve.
+// wd_part2d.cuh -- line passes of the fused 2-D pseudo step with the warp partition solve
+// (instantiated per precision in wd_part2d_f32.cu and wd_part2d_f64.cu).
 //
 // A block holds 8 grid lines of one direction in shared memory (staged with coalesced
 // loads: whole rows for direction 0, 32-byte segments of 8 neighbouring lines for
@@ -13,6 +14,8 @@
 // The passes compute exactly what the PCR passes of wd_fused2d.cu compute (the same row
 // formulas, the same tridiagonal systems, the same epilogues); only the elimination order
 // of the tridiagonal solves differs.
+#pragma once
+
 #include <algorithm>
 
 #include "wd_api_internal.h"
@@ -377,7 +380,7 @@ __global__ void __launch_bounds__(32 * LPB, P2_MINB(T, LPB)) k_p2_filter(F2Args<
 // Per-grid change norms from the block partials of the commit pass, in a fixed order: the
 // blocks of stacked grid k are the contiguous range [k * bpm, (k + 1) * bpm); a group of
 // tpm threads (a power of two, >= 32) reduces one grid at a time.
-__global__ void __launch_bounds__(1024) k_p2_reduce(const double* __restrict__ partial, int nblocks,
+static __global__ void __launch_bounds__(1024) k_p2_reduce(const double* __restrict__ partial, int nblocks,
                                                     int batch, double* result)
 {
     __shared__ double s_ss[32], s_mx[32];
@@ -528,6 +531,7 @@ cudaError_t p2_launch(const F2Args<T, M>& a, const PartTab<T>& tb, int which, in
     case 16: return p2_launch_r<T, M, 16>(a, tb, which, dir, st);
     case 17: return p2_launch_r<T, M, 17>(a, tb, which, dir, st);
     case 32: return p2_launch_r<T, M, 32>(a, tb, which, dir, st);
+    case 33: return p2_launch_r<T, M, 33>(a, tb, which, dir, st);
     default: return cudaErrorNotSupported;
     }
 }
@@ -546,12 +550,5 @@ bool p2_supported(const F2Args<T, M>& a, const PartTab<T>& tb, int which, int di
     }
     return true;
 }
-
-template cudaError_t p2_launch<double, double>(const F2Args<double, double>&, const PartTab<double>&, int,
-                                               int, cudaStream_t);
-template cudaError_t p2_launch<float, float>(const F2Args<float, float>&, const PartTab<float>&, int, int,
-                                             cudaStream_t);
-template bool p2_supported<double, double>(const F2Args<double, double>&, const PartTab<double>&, int, int);
-template bool p2_supported<float, float>(const F2Args<float, float>&, const PartTab<float>&, int, int);
 
 }  // namespace wd

@@ -1,0 +1,10 @@
+// wd_part2d_f64.cu -- FP64 instantiations of the warp partition passes (wd_part2d.cuh).
+#include "wd_part2d.cuh"
+
+namespace wd {
+
+template cudaError_t p2_launch<double, double>(const F2Args<double, double>&, const PartTab<double>&, int,
+                                               int, cudaStream_t);
+template bool p2_supported<double, double>(const F2Args<double, double>&, const PartTab<double>&, int, int);
+
+}  // namespace wd
