@@ -440,6 +440,27 @@ struct Solver {
         return WD_OK;
     }
 
+    // the boundary conditions of bc() for a single 2-D grid whose interior Dirichlet nodes are
+    // already reset (after a Cartesian stage): one launch
+    wd_status bc_faces2d(T* phi, bool poisson)
+    {
+        int klo[2], khi[2];
+        const double *rlo[2], *rhi[2];
+        for (int d = 0; d < 2; d++) {
+            klo[d] = g->desc.bc_lo[d];
+            khi[d] = g->desc.bc_hi[d];
+            if (poisson) {
+                if (klo[d] == WD_BC_FARFIELD) klo[d] = WD_BC_NEUMANN;
+                if (khi[d] == WD_BC_FARFIELD) khi[d] = WD_BC_NEUMANN;
+            }
+            rlo[d] = g->ffr + (2 * d) * g->fmax;
+            rhi[d] = g->ffr + (2 * d + 1) * g->fmax;
+        }
+        ProfScope ps(g, WD_K_BC);
+        CK(launch_bc_faces2d<T>(D, klo, khi, rlo, rhi, g->mask, (const T*)g->dval, poisson, phi, st));
+        return WD_OK;
+    }
+
     StageArgs<T, M> stage_args(const T* src, T* dst, bool poisson, const T* lad)
     {
         StageArgs<T, M> a;
@@ -696,7 +717,10 @@ struct Solver {
                 ProfScope ps(g, WD_K_POINT);
                 CK(c3_launch<T>(a, C3_S, st));
             }
-            if (faces_need_bc()) ST(bc(W(W_PHIS), poisson));
+            if (faces_need_bc()) {
+                if (D.ndim == 2) ST(bc_faces2d(W(W_PHIS), poisson));
+                else ST(bc(W(W_PHIS), poisson));
+            }
         }
         // filter along 0, 1 and 2 with the warp partition passes; the direction-2 pass also
         // resets the Dirichlet nodes, reduces the change norms and commits

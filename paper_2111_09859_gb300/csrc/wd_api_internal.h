@@ -61,6 +61,10 @@ template <typename T>
 cudaError_t launch_bc_face(const Dims& D, int dir, int kind_lo, int kind_hi, const double* rlo,
                            const double* rhi, T* phi, cudaStream_t st);
 template <typename T>
+cudaError_t launch_bc_faces2d(const Dims& D, const int* klo, const int* khi, const double* const* rlo,
+                              const double* const* rhi, const uint8_t* mask, const T* dval, int poisson, T* phi,
+                              cudaStream_t st);
+template <typename T>
 cudaError_t launch_bc_mask(const Dims& D, const uint8_t* mask, const T* dval, T* phi,
                            cudaStream_t st);
 template <typename T>

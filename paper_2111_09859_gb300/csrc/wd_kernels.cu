@@ -359,6 +359,84 @@ cudaError_t launch_spalding(const Dims& D, const T* const* U, const T* phip, T* 
 // boundary conditions
 // ------------------------------------------------------------------------------------
 
+// Both directions' far-field / Neumann faces of a single 2-D grid in one launch, with the
+// result of the two direction passes followed by the Dirichlet reset of the face nodes
+// (interior nodes must already hold their Dirichlet values).  Direction-1 face nodes at the
+// corners re-evaluate the two direction-0 face values they extrapolate from; direction-0
+// threads leave the rows that a direction-1 face overwrites.
+template <typename T>
+__device__ __forceinline__ T face_value(int kind, T v1, T v2, double r)
+{
+    return kind == WD_BC_NEUMANN ? v1 : v1 + T(r) * (v1 - v2);
+}
+
+template <typename T>
+__global__ void k_bc_faces2d(Dims D, int klo0, int khi0, int klo1, int khi1, const double* __restrict__ r0lo,
+                             const double* __restrict__ r0hi, const double* __restrict__ r1lo,
+                             const double* __restrict__ r1hi, const uint8_t* __restrict__ mask,
+                             const T* __restrict__ dval, int poisson, T* phi)
+{
+    const int n0 = D.n[0], n1 = D.n[1];
+    const long long p1 = D.pitch;
+    auto act = [](int k) { return k == WD_BC_FARFIELD || k == WD_BC_NEUMANN; };
+    const bool f1lo = act(klo1), f1hi = act(khi1);
+    // direction-0 face value at row j (side 0: i = 0, side 1: i = n0 - 1), from interior values
+    auto v0 = [&](int side, int j) -> T {
+        const int kind = side ? khi0 : klo0;
+        const long long b = D.idx(side ? n0 - 1 : 0, j, 0);
+        const long long s = side ? -1 : 1;
+        return face_value<T>(kind, phi[b + s], phi[b + 2 * s], (side ? r0hi : r0lo)[j]);
+    };
+    const int nf0 = 2 * n1, nf1 = 2 * n0;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nf0 + nf1; e += gridDim.x * blockDim.x) {
+        if (e < nf0) {
+            const int side = e / n1, j = e - side * n1;
+            const int kind = side ? khi0 : klo0;
+            if (!act(kind)) continue;
+            if ((j == 0 && f1lo) || (j == n1 - 1 && f1hi)) continue;   // a direction-1 face wins
+            const long long b = D.idx(side ? n0 - 1 : 0, j, 0);
+            T v = v0(side, j);
+            if (mask[b]) v = poisson ? T(0) : dval[b];
+            phi[b] = v;
+        } else {
+            const int q = e - nf0, side = q / n0, i = q - side * n0;
+            const int kind = side ? khi1 : klo1;
+            if (!act(kind)) continue;
+            const int j = side ? n1 - 1 : 0, js = side ? -1 : 1;
+            const long long b = D.idx(i, j, 0);
+            T w1, w2;
+            if ((i == 0 && act(klo0)) || (i == n0 - 1 && act(khi0))) {
+                const int s0 = i == 0 ? 0 : 1;
+                w1 = v0(s0, j + js);
+                w2 = v0(s0, j + 2 * js);
+            } else {
+                w1 = phi[b + js * p1];
+                w2 = phi[b + 2 * js * p1];
+            }
+            T v = face_value<T>(kind, w1, w2, (side ? r1hi : r1lo)[i]);
+            if (mask[b]) v = poisson ? T(0) : dval[b];
+            phi[b] = v;
+        }
+    }
+}
+
+template <typename T>
+cudaError_t launch_bc_faces2d(const Dims& D, const int* klo, const int* khi, const double* const* rlo,
+                              const double* const* rhi, const uint8_t* mask, const T* dval, int poisson, T* phi,
+                              cudaStream_t st)
+{
+    const int n = 2 * (D.n[0] + D.n[1]);
+    k_bc_faces2d<T><<<(n + 255) / 256, 256, 0, st>>>(D, klo[0], khi[0], klo[1], khi[1], rlo[0], rhi[0], rlo[1],
+                                                     rhi[1], mask, dval, poisson, phi);
+    return cudaGetLastError();
+}
+template cudaError_t launch_bc_faces2d<float>(const Dims&, const int*, const int*, const double* const*,
+                                              const double* const*, const uint8_t*, const float*, int, float*,
+                                              cudaStream_t);
+template cudaError_t launch_bc_faces2d<double>(const Dims&, const int*, const int*, const double* const*,
+                                               const double* const*, const uint8_t*, const double*, int, double*,
+                                               cudaStream_t);
+
 template <typename T>
 __global__ void k_bc_face(Dims D, int d, int klo, int khi, const double* __restrict__ rlo,
                           const double* __restrict__ rhi, T* phi)
