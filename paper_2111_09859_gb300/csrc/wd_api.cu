@@ -585,9 +585,11 @@ struct Solver {
             a.dst = stage_dst(s);
             a.stage = s;
             {
+                // direction 1 first: the direction-0 pass combines both LAD terms and smooths
+                // them along its lines
                 ProfScope ps(g, WD_K_DERIV);
-                CK(p2_launch<T, M>(a, dt0, F2_DERIV, 0, st));
                 CK(p2_launch<T, M>(a, dt1, F2_DERIV, 1, st));
+                CK(p2_launch<T, M>(a, dt0, F2_DERIV, 0, st));
             }
             {
                 ProfScope ps(g, WD_K_DIV);

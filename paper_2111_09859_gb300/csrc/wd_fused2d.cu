@@ -203,7 +203,7 @@ __device__ __forceinline__ T f2_stage_value(const F2Args<T, M>& a, long long e, 
         const T tx = T(ux), ty = T(uy);
         const T g2 = tx * tx + ty * ty;
         gm = sqrt(g2);
-        const T ph = a.src[e];
+        const T ph = __ldg(a.src + e);   // the stage input is never the stage output
         const T php = ph > T(0) ? ph : T(0);
         if (a.equation == WD_HJ_STD) gam = T(a.eps) * php;                   // Eq. 6
         else if (a.equation == WD_HJ_LAD) {                                  // Eq. 7
@@ -457,7 +457,7 @@ cudaError_t f2_launch(F2Args<T, M> a, int which, cudaStream_t st)
     const Dims& D = a.D;
     if (which == F2_STAGE) {
         long long b = (D.total + 255) / 256;
-        if (b > 152 * 16) b = 152 * 16;
+        if (b > 152 * 64) b = 152 * 64;     // about one node per thread
         k_f2_stage<T, M><<<(int)b, 256, 0, st>>>(a);
         return cudaGetLastError();
     }

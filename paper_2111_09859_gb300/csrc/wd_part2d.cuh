@@ -178,19 +178,33 @@ __global__ void __launch_bounds__(32 * LPB, P2_MINB(T, LPB)) k_p2_deriv(F2Args<T
     }
     __syncthreads();
     T* Dout = dir == 0 ? a.D0 : a.D1;
-    T* Lout = dir == 0 ? a.L0 : a.L1;
     const long long tot = D.total;
+    if (dir == 1 || !a.lad) {
+        p2_nodes<LPB>(D, dir, q0, nl, [&](int l, int i, long long e) {
+            Dout[e] = Dv[l * Lay::LS + Lay::at(i)];
+            if (a.lad) {
+                const PView<T, R> v{Ph + l * Lay::LS, N, per};
+                a.L1[e] = T(__ldg(a.lads + (long long)tot + e) * M(d4_row(v, i)));
+            }
+        });
+        return;
+    }
+    // direction 0 after direction 1: C|s_0 d4_0 + s_1 d4_1| along the block's lines, then its
+    // Gaussian along direction 0 (the first half of the separable smoothing of Eq. 7)
+    T* Gb = Dv + LPB * Lay::LS;
     p2_nodes<LPB>(D, dir, q0, nl, [&](int l, int i, long long e) {
         Dout[e] = Dv[l * Lay::LS + Lay::at(i)];
-        if (a.lad) {
-            const PView<T, R> v{Ph + l * Lay::LS, N, per};
-            Lout[e] = T(__ldg(a.lads + (long long)dir * tot + e) * M(d4_row(v, i)));
-        }
+        const PView<T, R> v{Ph + l * Lay::LS, N, per};
+        const T v0 = T(__ldg(a.lads + e) * M(d4_row(v, i))) + a.L1[e];
+        Gb[l * Lay::LS + Lay::at(i)] = T(a.C_lad) * (v0 < T(0) ? -v0 : v0);
+    });
+    __syncthreads();
+    p2_nodes<LPB>(D, dir, q0, nl, [&](int l, int i, long long e) {
+        a.G0[e] = gauss_rhs(PView<T, R>{Gb + l * Lay::LS, N, per}, i);
     });
 }
 
 // ---- B: metric-weighted divergence parts along one direction ------------------------------
-// (direction 0 also smooths C|LAD| along its lines, the first half of the Gaussian)
 template <typename T, typename M, int NF, int R, int LPB>
 __global__ void __launch_bounds__(32 * LPB, P2_MINB_DIV(T, LPB)) k_p2_div(F2Args<T, M> a, PartTab<T> tb, int dir)
 {
@@ -198,12 +212,10 @@ __global__ void __launch_bounds__(32 * LPB, P2_MINB_DIV(T, LPB)) k_p2_div(F2Args
     using Lay = PLayout<R>;
     constexpr int BUF = LPB * Lay::LS;
     T* U = reinterpret_cast<T*>(smraw);
-    T* G = U + NF * BUF;
     const Dims& D = a.D;
     const int N = D.n[dir], per = D.per[dir];
     const int q0 = blockIdx.x * LPB, nl = min(LPB, D.nlines(dir) - q0);
     const long long tot = D.total;
-    const bool gauss = dir == 0 && a.lad;
     p2_nodes<LPB>(D, dir, q0, nl, [&](int l, int i, long long e) {
         const int s = l * Lay::LS + Lay::at(i);
         const M d0 = M(a.D0[e]), d1 = M(a.D1[e]);
@@ -215,10 +227,6 @@ __global__ void __launch_bounds__(32 * LPB, P2_MINB_DIV(T, LPB)) k_p2_div(F2Args
             const M ig = M(1) / (sqrt(ux * ux + uy * uy) + M(a.eps0));
             U[2 * BUF + s] = T(ux * ig);
             U[3 * BUF + s] = T(uy * ig);
-        }
-        if (gauss) {
-            const T v = a.L0[e] + a.L1[e];
-            G[s] = T(a.C_lad) * (v < T(0) ? -v : v);
         }
     });
     __syncthreads();
@@ -262,7 +270,6 @@ __global__ void __launch_bounds__(32 * LPB, P2_MINB_DIV(T, LPB)) k_p2_div(F2Args
         const M x1 = __ldg(a.xi + (long long)(dir * 3 + 1) * tot + e);
         lap[e] = T(x0 * M(U[s]) + x1 * M(U[BUF + s]));
         if (NF == 4) kap[e] = T(x0 * M(U[2 * BUF + s]) + x1 * M(U[3 * BUF + s]));
-        if (gauss) a.G0[e] = gauss_rhs(PView<T, R>{G + l * Lay::LS, N, per}, i);
     });
 }
 
@@ -441,8 +448,8 @@ static size_t p2_ls(int R)
 // shared-memory buffers (lines x LS) of each pass
 static int p2_bufs(int which, int dir, bool curv, bool lad)
 {
-    if (which == F2_DERIV) return 2;
-    if (which == F2_DIV) return (curv ? 4 : 2) + (dir == 0 && lad ? 1 : 0);
+    if (which == F2_DERIV) return 2 + (dir == 0 && lad ? 1 : 0);
+    if (which == F2_DIV) return curv ? 4 : 2;
     if (which == F2_FILTER) return 3;   // field, old state, Dirichlet flags (rounded up)
     return 1;
 }
@@ -542,7 +549,7 @@ bool p2_supported(const F2Args<T, M>& a, const PartTab<T>& tb, int which, int di
 {
     if (!tb.ok) return false;
     const int lpb = p2_lpb(which, dir);
-    const int bufs = which == F2_DIV ? 5 : p2_bufs(which, dir, false, false);
+    const int bufs = which == F2_DIV ? 4 : (which == F2_DERIV ? 3 : p2_bufs(which, dir, false, false));
     if ((size_t)bufs * lpb * p2_ls(tb.R) * sizeof(T) > P2_SMEM_LIMIT) return false;
     if (which == F2_FILTER) {
         const int nb = (a.D.nlines(dir) + lpb - 1) / lpb;
