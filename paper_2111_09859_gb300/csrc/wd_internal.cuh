@@ -97,7 +97,7 @@ struct HostLineTab {
     size_t bytes = 0;
     double key = 0.0;         // alpha_f the table was built for (filters)
     int valid = 0;
-    // partition tables (pok = 0 when the line is not supported: N > 1056, R < 2, or a
+    // partition tables (pok = 0 when the line is not supported: N > 2048, R < 2, or a
     // periodic N that is not 32 R)
     int pR = 0, pok = 0;
     double* pdtab = nullptr;

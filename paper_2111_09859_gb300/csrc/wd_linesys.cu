@@ -252,7 +252,7 @@ void free_line_table(HostLineTab& tab)
 // rows per lane of the partition solve for a line of N rows (0: not supported)
 int part_rows(int N, int periodic)
 {
-    static const int Rs[] = {3, 4, 5, 8, 9, 16, 17, 32, 33};
+    static const int Rs[] = {3, 4, 5, 8, 9, 16, 17, 32, 33, 64};
     for (int R : Rs) {
         if (periodic ? N == 32 * R : N <= 32 * R) return R;
     }

@@ -512,17 +512,25 @@ static cudaError_t p2_launch_rl_filter(const F2Args<T, M>& a, const PartTab<T>& 
 // lines per block of a pass: 8 (whole rows for direction 0, 32-byte row segments of 8
 // neighbouring lines otherwise); the direction-2 filter of 3-D grids, whose rows lie a
 // whole plane apart, takes 32 lines for full 128-byte segments
-static int p2_lpb(int which, int dir) { return (dir == 2 && (which == F2_FILTER || which == P2_FILTER0)) ? 32 : 8; }
+static int p2_lpb(int which, int dir, int R)
+{
+    if (R > 33) return 4;   // 2048-node lines: the shared-memory budget allows 4 per block
+    return (dir == 2 && (which == F2_FILTER || which == P2_FILTER0)) ? 32 : 8;
+}
 
 template <typename T, typename M, int R>
 static cudaError_t p2_launch_r(const F2Args<T, M>& a, const PartTab<T>& tb, int which, int dir,
                                cudaStream_t st)
 {
-    if (p2_lpb(which, dir) == 32) {
-        if (which == F2_DERIV || which == F2_DIV) return cudaErrorNotSupported;
-        return p2_launch_rl_filter<T, M, R, 32>(a, tb, which, dir, st);
+    if constexpr (R > 33) {
+        return p2_launch_rl<T, M, R, 4>(a, tb, which, dir, st);
+    } else {
+        if (p2_lpb(which, dir, R) == 32) {
+            if (which == F2_DERIV || which == F2_DIV) return cudaErrorNotSupported;
+            return p2_launch_rl_filter<T, M, R, 32>(a, tb, which, dir, st);
+        }
+        return p2_launch_rl<T, M, R, 8>(a, tb, which, dir, st);
     }
-    return p2_launch_rl<T, M, R, 8>(a, tb, which, dir, st);
 }
 
 template <typename T, typename M>
@@ -539,6 +547,7 @@ cudaError_t p2_launch(const F2Args<T, M>& a, const PartTab<T>& tb, int which, in
     case 17: return p2_launch_r<T, M, 17>(a, tb, which, dir, st);
     case 32: return p2_launch_r<T, M, 32>(a, tb, which, dir, st);
     case 33: return p2_launch_r<T, M, 33>(a, tb, which, dir, st);
+    case 64: return p2_launch_r<T, M, 64>(a, tb, which, dir, st);
     default: return cudaErrorNotSupported;
     }
 }
@@ -548,7 +557,7 @@ template <typename T, typename M>
 bool p2_supported(const F2Args<T, M>& a, const PartTab<T>& tb, int which, int dir)
 {
     if (!tb.ok) return false;
-    const int lpb = p2_lpb(which, dir);
+    const int lpb = p2_lpb(which, dir, tb.R);
     const int bufs = which == F2_DIV ? 4 : (which == F2_DERIV ? 3 : p2_bufs(which, dir, false, false));
     if ((size_t)bufs * lpb * p2_ls(tb.R) * sizeof(T) > P2_SMEM_LIMIT) return false;
     if (which == F2_FILTER) {
