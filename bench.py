@@ -113,27 +113,28 @@ def peak_hbm():
 
 
 # DRAM bytes (read + write) per launch of the kernel classes of this workload, from one ncu
-# capture of the current kernels (k_p2_div direction 0: 69.8 MB, direction 1: 52.2 MB).
-# Writes below the algorithmic count stay in L2 for the next pass.
-PROFILED_TRAFFIC = {"div": 61.0e6}
+# capture of the current kernels (k_p2_div direction 0: 50.9 MB, direction 1: 51.7 MB).
+# Reads below the algorithmic count hit L2 (D_0, D_1 were just written); writes stay in L2
+# for the next pass.
+PROFILED_TRAFFIC = {"div": 51.3e6}
 
 
 def algorithmic_bytes(cls, nodes, nd, es, ms, curv, lad=True):
     """Algorithmic DRAM bytes of one launch of a kernel class of the fused 2-D step (every
     array a pass must touch read once, every output written once; one launch = one grid
     direction for the line passes):
-      deriv  phi in, d(phi)/dxi_l out; LAD: s_l in, s_l d4_l(phi) out
-      div    D_0, D_1 and the 4 metrics of U in, the divergence part(s) out; the
-             direction-0 launch (half of them) also reads both LAD terms and writes their
-             smoothed sum
+      deriv  phi in, d(phi)/dxi_l out; LAD: s_l in and, for direction 1, s_1 d4_1(phi)
+             out; direction 0 (half of the launches) reads it back and writes the smoothed
+             C|LAD| instead
+      div    D_0, D_1 and the 4 metrics of U in, the divergence part(s) out
       point  stage kernel: 13 state-size arrays in, the stage value and the RK4
              accumulator out, plus the Dirichlet flags
       filter / norm: the field in and out (norm: plus the old state and the flags)"""
     if cls == "deriv":
-        return nodes * (2 * es + ((es + ms) if lad else 0))
+        return int(nodes * (2 * es + ((1.5 * es + ms) if lad else 0)))
     if cls == "div":
         nout = 2 if curv else 1
-        return int(nodes * (2 * es + 4 * ms + nout * es + (1.5 * es if lad else 0)))
+        return int(nodes * (2 * es + 4 * ms + nout * es))
     if cls == "point":
         return nodes * (15 * es + 1)
     if cls == "filter":
