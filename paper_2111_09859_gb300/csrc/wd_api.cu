@@ -712,8 +712,7 @@ struct Solver {
             }
             if (a.lad) {
                 ProfScope ps(g, WD_K_GAUSS);
-                CK(c3_launch<T>(a, C3_GX, st));
-                if (D.ndim == 3) CK(c3_launch<T>(a, C3_GY, st));
+                CK(c3_launch<T>(a, D.ndim == 3 ? C3_GXY : C3_GX, st));
             }
             {
                 ProfScope ps(g, WD_K_POINT);

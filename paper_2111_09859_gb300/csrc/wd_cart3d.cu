@@ -3,10 +3,9 @@
 //     U_l = D_l(phi) / h_l,   lap(phi) = sum_l D_l(U_l) / h_l   (Eq. 9 with diagonal metrics),
 //     LAD term (Eq. 7) = C | sum_l d4_l(phi) s_l |   (s_l = h_l^(exponent - 4)),
 // and every pass is a stencil along grid lines read straight from global memory (L1/L2 serve
-// the neighbours).  One RK stage = four launches in 3-D (three in 2-D, without GY):
+// the neighbours).  One RK stage = three launches:
 //   U   U_0, U_1, U_2 and the raw LAD term,
-//   GX  Gaussian of the LAD term along direction 0,
-//   GY  Gaussian along direction 1,
+//   GXY Gaussian of the LAD term along directions 0 and 1 (one tiled pass; in 2-D: GX, along 0),
 //   S   Gaussian along direction 2, Laplacian, Gamma, right-hand side, local time step, RK4
 //       stage and the Dirichlet reset.
 // Threads are laid out as the grid (x fastest, 32 x 8 per block, one z plane per block row
@@ -190,6 +189,60 @@ __global__ void __launch_bounds__(256) k_c3_gauss(C3Args<T> a, int d, const T* _
     out[q.e] = g;
 }
 
+// Gaussians along directions 0 and 1 in one pass: a 32 x 32 tile of one z plane loads the LAD
+// term with a halo of 4 nodes (wrapped on periodic directions, reflected at the others),
+// smooths along x into shared memory for the tile's rows and the 4 halo rows on either side,
+// then along y; the result equals the two separate passes.
+template <typename T>
+__device__ __forceinline__ int halo_index(int u, int N, int per)
+{
+    if (per) return u < 0 ? u + N : (u >= N ? u - N : u);
+    u = u < 0 ? -u : u;
+    return u > N - 1 ? 2 * (N - 1) - u : u;
+}
+
+constexpr int GXY_TY = 32;   // tile rows (4 per thread of a 32 x 8 block)
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_c3_gauss_xy(C3Args<T> a)
+{
+    __shared__ T Ls[GXY_TY + 8][41];
+    __shared__ T Gx[GXY_TY + 8][33];
+    const Dims& D = a.D;
+    const int i0 = blockIdx.x * 32, j0 = blockIdx.y * GXY_TY, k = blockIdx.z;
+    const int tid = threadIdx.y * 32 + threadIdx.x;
+    const int st1 = D.pitch, st2 = D.pitch * D.n[1];
+    const T* Lk = a.L + (size_t)st2 * k;
+    // halo columns of this thread (fixed over the rows it loads)
+    for (int q = tid; q < (GXY_TY + 8) * 40; q += 256) {
+        const int r = q / 40, c = q - r * 40;
+        const int gi = halo_index<T>(i0 - 4 + c, D.n[0], D.per[0]);
+        const int gj = halo_index<T>(j0 - 4 + r, D.n[1], D.per[1]);
+        Ls[r][c] = __ldg(Lk + gi + st1 * gj);
+    }
+    __syncthreads();
+    const T c0 = T(3565.0 / 10368.0), c1 = T(3091.0 / 12960.0), c2 = T(1997.0 / 25920.0), c3 = T(149.0 / 12960.0),
+            c4 = T(107.0 / 103680.0);
+    for (int q = tid; q < (GXY_TY + 8) * 32; q += 256) {
+        const int r = q >> 5, c = q & 31;
+        const T* v = &Ls[r][c];
+        Gx[r][c] = c0 * v[4] + c1 * (v[5] + v[3]) + c2 * (v[6] + v[2]) + c3 * (v[7] + v[1]) + c4 * (v[8] + v[0]);
+    }
+    __syncthreads();
+    const int i = i0 + threadIdx.x;
+    if (i >= D.n[0]) return;
+    const int c = threadIdx.x;
+#pragma unroll
+    for (int rr = 0; rr < GXY_TY / 8; rr++) {
+        const int j = j0 + threadIdx.y + 8 * rr;
+        if (j >= D.n[1]) break;
+        const int r = threadIdx.y + 8 * rr + 4;
+        const T g = c0 * Gx[r][c] + c1 * (Gx[r + 1][c] + Gx[r - 1][c]) + c2 * (Gx[r + 2][c] + Gx[r - 2][c]) +
+                    c3 * (Gx[r + 3][c] + Gx[r - 3][c]) + c4 * (Gx[r + 4][c] + Gx[r - 4][c]);
+        a.G2[i + st1 * j + (size_t)st2 * k] = g;
+    }
+}
+
 // EQ: 0 Poisson, 1 standard HJ, 2 LAD HJ, 3 eikonal (Gamma = 0)
 template <typename T, int ND, int SCH, int EQ>
 __global__ void __launch_bounds__(256) k_c3_stage(C3Args<T> a)
@@ -298,7 +351,11 @@ cudaError_t c3_launch(const C3Args<T>& a, int which, cudaStream_t st)
 {
     const dim3 blk(32, 8, 1);
     const dim3 grd((a.D.n[0] + 31) / 32, (a.D.n[1] + 7) / 8, a.D.n[2]);
-    if (which == C3_GX) k_c3_gauss<T><<<grd, blk, 0, st>>>(a, 0, a.L, a.G1);
+    if (which == C3_GXY) {
+        const dim3 g2((a.D.n[0] + 31) / 32, (a.D.n[1] + GXY_TY - 1) / GXY_TY, a.D.n[2]);
+        k_c3_gauss_xy<T><<<g2, blk, 0, st>>>(a);
+    }
+    else if (which == C3_GX) k_c3_gauss<T><<<grd, blk, 0, st>>>(a, 0, a.L, a.G1);
     else if (which == C3_GY) k_c3_gauss<T><<<grd, blk, 0, st>>>(a, 1, a.G1, a.G2);
     else if (a.D.ndim == 3) c3_launch_nd<T, 3>(a, which, grd, blk, st);
     else c3_launch_nd<T, 2>(a, which, grd, blk, st);

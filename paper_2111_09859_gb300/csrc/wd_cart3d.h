@@ -5,7 +5,7 @@
 
 namespace wd {
 
-enum { C3_U = 0, C3_GX = 1, C3_GY = 2, C3_S = 3 };
+enum { C3_U = 0, C3_GX = 1, C3_GY = 2, C3_S = 3, C3_GXY = 4 };
 
 template <typename T>
 struct C3Args {
