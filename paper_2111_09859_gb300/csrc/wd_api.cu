@@ -580,6 +580,7 @@ struct Solver {
     wd_status step_part2d(F2Args<T, M>& a)
     {
         const PartTab<T> dt0 = g->dtab[0].template pview<T>(), dt1 = g->dtab[1].template pview<T>();
+        bool merged_div = true;
         for (int s = 0; s < 4; s++) {
             a.src = stage_src(s);
             a.dst = stage_dst(s);
@@ -593,8 +594,15 @@ struct Solver {
             }
             {
                 ProfScope ps(g, WD_K_DIV);
-                CK(p2_launch<T, M>(a, dt0, F2_DIV, 0, st));
-                CK(p2_launch<T, M>(a, dt1, F2_DIV, 1, st));
+                const cudaError_t e = merged_div ? p2_div2<T, M>(a, dt0, dt1, st) : cudaErrorNotSupported;
+                if (e == cudaErrorNotSupported) {
+                    cudaGetLastError();
+                    merged_div = false;
+                    CK(p2_launch<T, M>(a, dt0, F2_DIV, 0, st));
+                    CK(p2_launch<T, M>(a, dt1, F2_DIV, 1, st));
+                } else {
+                    CK(e);
+                }
             }
             {
                 ProfScope ps(g, WD_K_POINT);

@@ -52,5 +52,8 @@ template <typename T, typename M>
 cudaError_t p2_launch(const F2Args<T, M>& a, const PartTab<T>& tb, int which, int dir, cudaStream_t st);
 template <typename T, typename M>
 bool p2_supported(const F2Args<T, M>& a, const PartTab<T>& tb, int which, int dir);
+// both directions' F2_DIV passes in one launch (cudaErrorNotSupported for other line pairs)
+template <typename T, typename M>
+cudaError_t p2_div2(const F2Args<T, M>& a, const PartTab<T>& t0, const PartTab<T>& t1, cudaStream_t st);
 
 }  // namespace wd

@@ -206,15 +206,15 @@ __global__ void __launch_bounds__(32 * LPB, P2_MINB(T, LPB)) k_p2_deriv(F2Args<T
 
 // ---- B: metric-weighted divergence parts along one direction ------------------------------
 template <typename T, typename M, int NF, int R, int LPB>
-__global__ void __launch_bounds__(32 * LPB, P2_MINB_DIV(T, LPB)) k_p2_div(F2Args<T, M> a, PartTab<T> tb, int dir)
+__device__ __forceinline__ void p2_div_body(const F2Args<T, M>& a, const PartTab<T>& tb, int dir, int bid,
+                                            unsigned char* smraw)
 {
-    extern __shared__ __align__(16) unsigned char smraw[];
     using Lay = PLayout<R>;
     constexpr int BUF = LPB * Lay::LS;
     T* U = reinterpret_cast<T*>(smraw);
     const Dims& D = a.D;
     const int N = D.n[dir], per = D.per[dir];
-    const int q0 = blockIdx.x * LPB, nl = min(LPB, D.nlines(dir) - q0);
+    const int q0 = bid * LPB, nl = min(LPB, D.nlines(dir) - q0);
     const long long tot = D.total;
     p2_nodes<LPB>(D, dir, q0, nl, [&](int l, int i, long long e) {
         const int s = l * Lay::LS + Lay::at(i);
@@ -271,6 +271,23 @@ __global__ void __launch_bounds__(32 * LPB, P2_MINB_DIV(T, LPB)) k_p2_div(F2Args
         lap[e] = T(x0 * M(U[s]) + x1 * M(U[BUF + s]));
         if (NF == 4) kap[e] = T(x0 * M(U[2 * BUF + s]) + x1 * M(U[3 * BUF + s]));
     });
+}
+
+template <typename T, typename M, int NF, int R, int LPB>
+__global__ void __launch_bounds__(32 * LPB, P2_MINB_DIV(T, LPB)) k_p2_div(F2Args<T, M> a, PartTab<T> tb, int dir)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    p2_div_body<T, M, NF, R, LPB>(a, tb, dir, blockIdx.x, smraw);
+}
+
+// both directions' divergence passes in one launch (blocks [0, nb0) direction 0, the rest
+// direction 1), so that the two passes fill each other's partial last waves
+template <typename T, typename M, int NF, int R0, int R1>
+__global__ void __launch_bounds__(256, P2_MINB_DIV(T, 8)) k_p2_div2(F2Args<T, M> a, PartTab<T> t0, PartTab<T> t1, int nb0)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    if ((int)blockIdx.x < nb0) p2_div_body<T, M, NF, R0, 8>(a, t0, 0, blockIdx.x, smraw);
+    else p2_div_body<T, M, NF, R1, 8>(a, t1, 1, blockIdx.x - nb0, smraw);
 }
 
 // ---- F: filter along one direction; direction 1 with commit = 1 also applies the line
@@ -550,6 +567,36 @@ cudaError_t p2_launch(const F2Args<T, M>& a, const PartTab<T>& tb, int which, in
     case 64: return p2_launch_r<T, M, 64>(a, tb, which, dir, st);
     default: return cudaErrorNotSupported;
     }
+}
+
+template <typename T, typename M, int R0, int R1>
+static cudaError_t p2_div2_rr(const F2Args<T, M>& a, const PartTab<T>& t0, const PartTab<T>& t1, cudaStream_t st)
+{
+    const Dims& D = a.D;
+    const bool curv = a.curvature && !a.poisson;
+    const int nf = curv ? 4 : 2;
+    const int nb0 = (D.nlines(0) + 7) / 8, nb1 = (D.nlines(1) + 7) / 8;
+    const size_t sm0 = (size_t)nf * 8 * PLayout<R0>::LS * sizeof(T), sm1 = (size_t)nf * 8 * PLayout<R1>::LS * sizeof(T);
+    const size_t sm = sm0 > sm1 ? sm0 : sm1;
+    if (sm > P2_SMEM_LIMIT) return cudaErrorNotSupported;
+    static bool attr = false;
+    if (!attr) p2_allow(k_p2_div2<T, M, 2, R0, R1>), p2_allow(k_p2_div2<T, M, 4, R0, R1>), attr = true;
+    if (curv) k_p2_div2<T, M, 4, R0, R1><<<nb0 + nb1, 256, sm, st>>>(a, t0, t1, nb0);
+    else k_p2_div2<T, M, 2, R0, R1><<<nb0 + nb1, 256, sm, st>>>(a, t0, t1, nb0);
+    return cudaGetLastError();
+}
+
+// both divergence passes in one launch for the line-length pairs of the O-grid sizes
+// (periodic 128 .. 1024 around, 65 .. 513 radial); cudaErrorNotSupported otherwise
+template <typename T, typename M>
+cudaError_t p2_div2(const F2Args<T, M>& a, const PartTab<T>& t0, const PartTab<T>& t1, cudaStream_t st)
+{
+    if (!t0.ok || !t1.ok) return cudaErrorNotSupported;
+    if (t0.R == 16 && t1.R == 9) return p2_div2_rr<T, M, 16, 9>(a, t0, t1, st);
+    if (t0.R == 4 && t1.R == 3) return p2_div2_rr<T, M, 4, 3>(a, t0, t1, st);
+    if (t0.R == 8 && t1.R == 5) return p2_div2_rr<T, M, 8, 5>(a, t0, t1, st);
+    if (t0.R == 32 && t1.R == 17) return p2_div2_rr<T, M, 32, 17>(a, t0, t1, st);
+    return cudaErrorNotSupported;
 }
 
 // whether the pass `which` (F2_DERIV, F2_DIV, P2_FILTER0 or F2_FILTER) fits direction dir

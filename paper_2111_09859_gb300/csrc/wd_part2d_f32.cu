@@ -7,4 +7,7 @@ template cudaError_t p2_launch<float, float>(const F2Args<float, float>&, const 
                                              cudaStream_t);
 template bool p2_supported<float, float>(const F2Args<float, float>&, const PartTab<float>&, int, int);
 
+template cudaError_t p2_div2<float, float>(const F2Args<float, float>&, const PartTab<float>&, const PartTab<float>&,
+                                         cudaStream_t);
+
 }  // namespace wd

@@ -7,4 +7,7 @@ template cudaError_t p2_launch<double, double>(const F2Args<double, double>&, co
                                                int, cudaStream_t);
 template bool p2_supported<double, double>(const F2Args<double, double>&, const PartTab<double>&, int, int);
 
+template cudaError_t p2_div2<double, double>(const F2Args<double, double>&, const PartTab<double>&, const PartTab<double>&,
+                                         cudaStream_t);
+
 }  // namespace wd
