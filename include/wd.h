@@ -247,6 +247,14 @@ wd_status wd_change_norms_noalloc(const void* new_dev, const void* old_dev,
                                   const uint8_t* mask_dev, long long n, int precision,
                                   double scale, double* norms_dev, void* cuda_stream);
 
+/* Launch shapes chosen by the autotuner for this grid (0: not tuned, the default shape):
+ * the block size of the pointwise stage kernel of the fused 2-D path and the block rows of
+ * the Cartesian stencil kernels.  Before a grid's first pseudo step the library times the
+ * candidate shapes (128 / 256 / 512 threads; 4 / 8 / 16 rows of 32) on the grid's own arrays
+ * and keeps the fastest, cached per grid shape for the process; the shapes do not change
+ * results.  The environment variable WD_AUTOTUNE=0 disables it. */
+wd_status wd_get_tuning(wd_grid g, int* stage_threads, int* stencil_rows);
+
 /* ---- geometry reuse ---------------------------------------------------------------- */
 
 /* Replaces the coordinates and the caller Dirichlet set of an existing grid without any

@@ -5,10 +5,13 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <string>
 #include <type_traits>
+#include <map>
+#include <mutex>
 #include <vector>
 
 #include "wd_api_internal.h"
@@ -83,6 +86,9 @@ struct wd_grid_s {
     int npartial = 0;           // capacity of `partial` in blocks
     int force_generic = 0;      // WD_FORCE_GENERIC=1 at creation: never use the fused path
     int part_off = 0;           // WD_PART_OFF=1 at creation: fused 2-D path with PCR passes
+    int tuned = 0;              // autotuner ran for this grid
+    int tune_stage_threads = 0; // chosen block size of the 2-D stage kernel (0: default)
+    int tune_by = 0;            // chosen block rows of the Cartesian stencil kernels (0: default)
     int cart = 0;               // uniform Cartesian 3-D grid (diagonal constant metrics)
     double h[3] = {0, 0, 0};    // its spacings
     HostLineTab dtab[3], ftab[3], etab[3];
@@ -278,6 +284,67 @@ static void release(wd_grid g)
     if (g->ev_out) cudaEventDestroy(g->ev_out);
     if (g->stream) cudaStreamDestroy(g->stream);
     delete g;
+}
+
+// ------------------------------------------------------------------------------------
+// autotuner: the launch shapes that do not change results (block size of the pointwise
+// stage kernel, block rows of the Cartesian stencil kernels) are timed on the grid's own
+// arrays before its first pseudo step and cached per grid shape for the process, so pooled
+// and served grids of a known shape start tuned.  WD_AUTOTUNE=0 keeps the defaults.
+// ------------------------------------------------------------------------------------
+static std::mutex g_tune_mu;
+static std::map<std::string, int> g_tune_cache;
+
+static bool autotune_enabled()
+{
+    const char* e = std::getenv("WD_AUTOTUNE");
+    return !(e && e[0] == '0');
+}
+
+// average device time of one call of fn on stream st (one untimed call first, then three)
+template <typename F>
+static float time_calls(cudaStream_t st, F&& fn)
+{
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        cudaGetLastError();
+        return INFINITY;
+    }
+    fn();
+    cudaEventRecord(e0, st);
+    for (int r = 0; r < 3; r++) fn();
+    cudaEventRecord(e1, st);
+    float ms = INFINITY;
+    if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+        cudaGetLastError();
+        ms = INFINITY;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return ms / 3.0f;
+}
+
+// the cached choice for key, else the fastest candidate (timed by time_of) stored under key
+template <typename F>
+static int tune_choice(const std::string& key, std::initializer_list<int> cand, F&& time_of)
+{
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) return it->second;
+    }
+    int best = *cand.begin();
+    float tb = INFINITY;
+    for (int c : cand) {
+        const float t = time_of(c);
+        if (t < tb) {
+            tb = t;
+            best = c;
+        }
+    }
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune_cache[key] = best;
+    return best;
 }
 
 // ------------------------------------------------------------------------------------
@@ -554,6 +621,7 @@ struct Solver {
         a.result = g->result;
         a.max_partials = g->npartial;
         a.batch = g->batch;
+        a.stage_threads = g->tune_stage_threads;
         return a;
     }
 
@@ -677,9 +745,8 @@ struct Solver {
         return false;
     }
 
-    wd_status step_cart3d(bool poisson)
+    C3Args<T> c3_args(bool poisson)
     {
-        if (p->filter) ST(ensure_filter(p->alpha_f));
         C3Args<T> a;
         std::memset(&a, 0, sizeof(a));
         a.D = D;
@@ -710,6 +777,14 @@ struct Solver {
         a.equation = p->equation;
         a.lad = p->equation == WD_HJ_LAD && !poisson;
         a.poisson = poisson;
+        a.by = g->tune_by;
+        return a;
+    }
+
+    wd_status step_cart3d(bool poisson)
+    {
+        if (p->filter) ST(ensure_filter(p->alpha_f));
+        C3Args<T> a = c3_args(poisson);
         for (int s = 0; s < 4; s++) {
             a.src = s == 0 ? W(W_PHIN) : W(W_PHIS);
             a.dst = W(W_PHIS);
@@ -917,8 +992,46 @@ struct Solver {
         return WD_OK;
     }
 
+    // times the free launch shapes of this grid's path once (see the autotuner above); stage
+    // 0 of every timed kernel overwrites its outputs, and the first pseudo step recomputes them
+    wd_status autotune()
+    {
+        if (g->tuned || g->prof_on || !autotune_enabled()) return WD_OK;
+        g->tuned = 1;
+        char key[160];
+        std::snprintf(key, sizeof(key), "%d:%dx%dx%d:p%d:s%d:e%d:c%d:%s", D.ndim, D.n[0], D.n[1], D.n[2],
+                      g->desc.precision, g->desc.scheme, p->equation, p->curvature,
+                      fused2d() ? "f2" : (cart3d() ? "c3" : "gen"));
+        if (fused2d()) {
+            if (p->equation == WD_HJ_LAD) ST(ensure_lads(p->lad_exp));
+            F2Args<T, M> a = f2_args(false);
+            a.src = W(W_PHIN);
+            a.dst = W(W_PHIS);
+            a.stage = 0;
+            g->tune_stage_threads = tune_choice(key, {128, 256, 512}, [&](int c) {
+                a.stage_threads = c;
+                return time_calls(st, [&] { f2_launch<T, M>(a, F2_STAGE, st); });
+            });
+        } else if (cart3d()) {
+            C3Args<T> a = c3_args(false);
+            a.src = W(W_PHIN);
+            a.dst = W(W_PHIS);
+            a.stage = 0;
+            g->tune_by = tune_choice(key, {4, 8, 16}, [&](int c) {
+                a.by = c;
+                return time_calls(st, [&] {
+                    c3_launch<T>(a, C3_U, st);
+                    c3_launch<T>(a, C3_S, st);
+                });
+            });
+        }
+        CK(cudaGetLastError());
+        return WD_OK;
+    }
+
     wd_status begin(const void* phi_user, bool warm)
     {
+        ST(autotune());
         R = Run();
         std::memset(&R.s, 0, sizeof(R.s));
         R.every = p->check_every > 0 ? p->check_every : 1;
@@ -1664,6 +1777,14 @@ wd_status wd_level_length(wd_grid g, const void* phi_dev, double level, double* 
     double sum = 0.0;
     for (int b = 0; b < nb; b++) sum += part[b];
     *length = sum;
+    return WD_OK;
+}
+
+wd_status wd_get_tuning(wd_grid g, int* stage_threads, int* stencil_rows)
+{
+    if (!g) return set_error(WD_ERR_INVALID_ARG, "grid is NULL");
+    if (stage_threads) *stage_threads = g->tune_stage_threads;
+    if (stencil_rows) *stencil_rows = g->tune_by;
     return WD_OK;
 }
 

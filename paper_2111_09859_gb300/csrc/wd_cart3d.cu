@@ -8,7 +8,7 @@
 //   GXY Gaussian of the LAD term along directions 0 and 1 (one tiled pass; in 2-D: GX, along 0),
 //   S   Gaussian along direction 2, Laplacian, Gamma, right-hand side, local time step, RK4
 //       stage and the Dirichlet reset.
-// Threads are laid out as the grid (x fastest, 32 x 8 per block, one z plane per block row
+// Threads are laid out as the grid (x fastest, 32 x by per block (by autotuned), one z plane per block row
 // of the launch), offsets are 32-bit, and a node whose stencil stays clear of the faces
 // takes a branch-free path; the boundary rows are those of the line passes.  The formulas
 // and the order of operations are those of the generic path.
@@ -128,7 +128,7 @@ __device__ __forceinline__ bool c3_node(const C3Args<T>& a, C3Node& q)
 {
     const Dims& D = a.D;
     q.c[0] = blockIdx.x * 32 + threadIdx.x;
-    q.c[1] = blockIdx.y * 8 + threadIdx.y;
+    q.c[1] = blockIdx.y * blockDim.y + threadIdx.y;
     q.c[2] = blockIdx.z;
     if (q.c[0] >= D.n[0] || q.c[1] >= D.n[1]) return false;
     q.st[0] = 1;
@@ -144,7 +144,7 @@ struct C3Half {
 };
 
 template <typename T, int ND, int SCH, int LAD>
-__global__ void __launch_bounds__(256) k_c3_u(C3Args<T> a)
+__global__ void __launch_bounds__(512) k_c3_u(C3Args<T> a)
 {
     C3Node q;
     if (!c3_node(a, q)) return;
@@ -172,7 +172,7 @@ __global__ void __launch_bounds__(256) k_c3_u(C3Args<T> a)
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_c3_gauss(C3Args<T> a, int d, const T* __restrict__ in, T* out)
+__global__ void __launch_bounds__(512) k_c3_gauss(C3Args<T> a, int d, const T* __restrict__ in, T* out)
 {
     C3Node q;
     if (!c3_node(a, q)) return;
@@ -245,7 +245,7 @@ __global__ void __launch_bounds__(256) k_c3_gauss_xy(C3Args<T> a)
 
 // EQ: 0 Poisson, 1 standard HJ, 2 LAD HJ, 3 eikonal (Gamma = 0)
 template <typename T, int ND, int SCH, int EQ>
-__global__ void __launch_bounds__(256) k_c3_stage(C3Args<T> a)
+__global__ void __launch_bounds__(512) k_c3_stage(C3Args<T> a)
 {
     C3Node q;
     if (!c3_node(a, q)) return;
@@ -349,11 +349,12 @@ static void c3_launch_nd(const C3Args<T>& a, int which, dim3 grd, dim3 blk, cuda
 template <typename T>
 cudaError_t c3_launch(const C3Args<T>& a, int which, cudaStream_t st)
 {
-    const dim3 blk(32, 8, 1);
-    const dim3 grd((a.D.n[0] + 31) / 32, (a.D.n[1] + 7) / 8, a.D.n[2]);
+    const int by = a.by > 0 ? a.by : 8;
+    const dim3 blk(32, by, 1);
+    const dim3 grd((a.D.n[0] + 31) / 32, (a.D.n[1] + by - 1) / by, a.D.n[2]);
     if (which == C3_GXY) {
         const dim3 g2((a.D.n[0] + 31) / 32, (a.D.n[1] + GXY_TY - 1) / GXY_TY, a.D.n[2]);
-        k_c3_gauss_xy<T><<<g2, blk, 0, st>>>(a);
+        k_c3_gauss_xy<T><<<g2, dim3(32, 8, 1), 0, st>>>(a);
     }
     else if (which == C3_GX) k_c3_gauss<T><<<grd, blk, 0, st>>>(a, 0, a.L, a.G1);
     else if (which == C3_GY) k_c3_gauss<T><<<grd, blk, 0, st>>>(a, 1, a.G1, a.G2);

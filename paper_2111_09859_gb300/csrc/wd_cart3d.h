@@ -25,6 +25,7 @@ struct C3Args {
     const T* dval;
     T eps, cfl, C_lad;
     int equation, lad, stage, poisson;
+    int by;                      // block rows of the stencil kernels (0: 8; autotuned)
 };
 
 template <typename T>

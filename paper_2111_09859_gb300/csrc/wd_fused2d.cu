@@ -264,7 +264,7 @@ __device__ __forceinline__ T f2_stage_value(const F2Args<T, M>& a, long long e, 
 }
 
 template <typename T, typename M>
-__global__ void __launch_bounds__(256) k_f2_stage(F2Args<T, M> a)
+__global__ void __launch_bounds__(512) k_f2_stage(F2Args<T, M> a)
 {
     const Dims& D = a.D;
     const int N1 = D.n[1];
@@ -456,9 +456,10 @@ cudaError_t f2_launch(F2Args<T, M> a, int which, cudaStream_t st)
 {
     const Dims& D = a.D;
     if (which == F2_STAGE) {
-        long long b = (D.total + 255) / 256;
+        const int thr = a.stage_threads > 0 ? a.stage_threads : 256;
+        long long b = (D.total + thr - 1) / thr;
         if (b > 152 * 64) b = 152 * 64;     // about one node per thread
-        k_f2_stage<T, M><<<(int)b, 256, 0, st>>>(a);
+        k_f2_stage<T, M><<<(int)b, thr, 0, st>>>(a);
         return cudaGetLastError();
     }
     const size_t es = sizeof(T);

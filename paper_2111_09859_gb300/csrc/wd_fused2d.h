@@ -40,6 +40,7 @@ struct F2Args {
     int max_partials;
     int batch;                           // stacked grids (n[2]); result holds 2 per grid
     int lpb[3], nb[3];                   // filled by the launcher
+    int stage_threads;                   // block size of the stage kernel (0: 256; autotuned)
 };
 
 template <typename T, typename M>

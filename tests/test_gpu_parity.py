@@ -396,3 +396,30 @@ def test_cartesian_2d_steps_with_neumann_faces(wd, oracle, generic, eq, monkeypa
     refp, _ = og.poisson_steps(np.zeros(spec.N), 10, **oracle_kw(1, prm))
     outp, _ = g.steps(gpu_params(wd, 1, prm), g.as_field(np.zeros(spec.N)), 10, kind=1)
     np.testing.assert_allclose(to_np(outp), refp, atol=1e-10 * scale(refp), rtol=0)
+
+
+@pytest.mark.parametrize("case", ["cylinder", "duct", "star"])
+def test_autotuned_shapes_do_not_change_results(wd, monkeypatch, case):
+    """The autotuner only picks launch shapes: solves with and without it are bit-identical,
+    and the chosen shapes are among the candidates."""
+    spec, scheme, prec, kw = {
+        "cylinder": (W.cylinder(65, 128, 1.1), 4, 1, dict(equation=1, curvature=1)),
+        "duct": (W.duct(32, nx=16), 2, 1, dict(equation=1)),
+        "star": (W.star(97), 1, 1, dict(equation=1, lad_exp=4.0, eps=0.15)),
+    }[case]
+    p = wd.default_params(scheme, tol_l2=1e-6, max_iters=400, **kw)
+    out = {}
+    for tune in ("0", "1"):
+        monkeypatch.setenv("WD_AUTOTUNE", tune)
+        g = wd.Grid(spec, prec, scheme)
+        phi, st = g.solve(p)
+        out[tune] = (to_np(phi), st["iters"], g.tuning())
+        g.close()
+    np.testing.assert_array_equal(out["0"][0], out["1"][0])
+    assert out["0"][1] == out["1"][1]
+    assert out["0"][2] == (0, 0)
+    threads, rows = out["1"][2]
+    if case == "cylinder":
+        assert threads in (128, 256, 512)
+    else:
+        assert rows in (4, 8, 16)
