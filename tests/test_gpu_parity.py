@@ -423,3 +423,20 @@ def test_autotuned_shapes_do_not_change_results(wd, monkeypatch, case):
         assert threads in (128, 256, 512)
     else:
         assert rows in (4, 8, 16)
+
+
+@pytest.mark.parametrize("scheme,prec,tol", [(1, 0, 1e-6), (4, 0, 1e-6), (1, 1, 2e-4)])
+def test_eikonal_full_solve(wd, oracle, scheme, prec, tol):
+    """Eikonal (Gamma = 0) full solves of the channel on the fused 2-D path against the
+    oracle at the parity bar."""
+    spec = W.channel(16, 65)
+    prm = base_params(scheme, equation=2)
+    og = oracle_grid(oracle, spec, scheme)
+    ref, ost = og.solve(**oracle_kw(scheme, prm))
+    g = wd.Grid(spec, prec, scheme)
+    p = gpu_params(wd, scheme, prm)
+    if prec != 0:
+        p.tol_l2 = 1e-7
+    phi, st = g.solve(p)
+    assert st["converged"] == 1
+    np.testing.assert_allclose(to_np(phi), ref, atol=tol, rtol=0)

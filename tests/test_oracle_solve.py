@@ -191,3 +191,24 @@ def test_ellipse_against_sampled_distance(oracle, aspect):
     err = np.abs(phi - sampled_ellipse_distance(sp))
     assert err.max() <= 1.5e-2
     assert np.sqrt((err ** 2).mean()) <= 5e-3
+
+
+@pytest.mark.parametrize("scheme", [0, 1, 4])
+def test_eikonal_channel_errors_where_fronts_meet(oracle, scheme):
+    """Eikonal with central schemes (Gamma = 0, filtered): the error peaks on the channel's
+    centre line, where the fronts from both walls meet, and HJ-LAD's global L2 error is below
+    the Eikonal one for the same scheme (tests/golden/paper_claims.json, eikonal_channel)."""
+    claim = GOLD["eikonal_channel"]
+    sp = W.channel(16, 65)
+    ex = np.minimum(sp.xyz[1], 1 - sp.xyz[1])
+    err = {}
+    for eq in (2, 1):
+        g = grid_of(oracle, sp, scheme)
+        phi, st = g.solve(equation=eq, scheme=scheme, cfl=0.8 if scheme < 3 else 0.6, tol_l2=1e-10,
+                          max_iters=20000, poisson_max_iters=100, alpha_f=0.49)
+        assert st["converged"]
+        err[eq] = np.abs(phi - ex).reshape(65, 16)
+    j = np.unravel_index(np.argmax(err[2]), err[2].shape)[0]
+    assert abs(j - 32) <= claim["centre_tolerance_nodes"]
+    l2 = {eq: np.sqrt((e ** 2).mean()) for eq, e in err.items()}
+    assert l2[1] < l2[2]
