@@ -28,7 +28,7 @@ _lock = threading.Lock()
 _lib = None
 
 BC_WALL, BC_FARFIELD, BC_NEUMANN, BC_PERIODIC = 0, 1, 2, 3
-E2, E4, E6, C4, C6 = 0, 1, 2, 3, 4
+E2, E4, E6, C4, C6, UW = 0, 1, 2, 3, 4, 5
 HJ_STD, HJ_LAD, EIKONAL = 0, 1, 2
 INIT_ZERO, INIT_POISSON, INIT_GIVEN = 0, 1, 2
 
@@ -99,6 +99,11 @@ def lib():
             L.or_solve.argtypes = [vp, C.POINTER(_Params), _DP, C.POINTER(_Stats)]
             L.or_tridiag.argtypes = [C.c_int, C.c_int, _DP, _DP, _DP, _DP, _DP]
             L.or_filter_coeffs.argtypes = [C.c_int, C.c_double, _DP]
+            L.or_upwind_advection.argtypes = [vp, _DP, _DP]
+            L.or_upwind_slope.restype = C.c_double
+            L.or_upwind_slope.argtypes = [C.c_double, C.c_double]
+            L.or_levelset_gradmag.argtypes = [vp, C.c_double, _DP, _DP]
+            L.or_levelset_steps.argtypes = [vp, C.c_double, C.c_double, _DP, C.c_int]
             _lib = L
     return _lib
 
@@ -231,6 +236,24 @@ class Grid:
         lib().or_poisson_steps(self._h, C.byref(p), a, int(n), C.byref(st))
         return a, _stats_dict(st)
 
+    def upwind_advection(self, phi):
+        """U.grad(phi) of the baseline upwind scheme (Eqs. UW1-UW5)."""
+        out = self._out()
+        lib().or_upwind_advection(self._h, _f64(phi), out)
+        return out
+
+    def levelset_gradmag(self, phi, F):
+        """|grad phi| from the upwind slopes, for a front of normal speed F."""
+        out = self._out()
+        lib().or_levelset_gradmag(self._h, float(F), _f64(phi), out)
+        return out
+
+    def levelset_steps(self, phi, F, dt, n):
+        """n RK4 steps of d(phi)/dt + F |grad phi| = 0 (Sec. 5.5) with time step dt."""
+        a = _f64(phi).copy()
+        lib().or_levelset_steps(self._h, float(F), float(dt), a, int(n))
+        return a
+
     def solve(self, phi=None, **params):
         a = np.zeros(self.N) if phi is None else _f64(phi).copy()
         st = _Stats()
@@ -251,6 +274,11 @@ def tridiag(a, b, c, d, cyclic=False):
     x = np.zeros(n)
     lib().or_tridiag(n, int(cyclic), _f64(a), _f64(b), _f64(c), _f64(d), x)
     return x
+
+
+def upwind_slope(B, F):
+    """The upwind slope of Eqs. UW3-UW5 from one backward and one forward difference."""
+    return lib().or_upwind_slope(float(B), float(F))
 
 
 def filter_coeffs(hw, alpha_f):

@@ -222,6 +222,7 @@ static void deriv_compact_1d(int scheme, int n, int periodic, const double* f, d
 
 static void deriv_1d(int scheme, int n, int periodic, const double* f, double* df)
 {
+    if (scheme == OR_UW) scheme = OR_E2;   /* the baseline's central terms (Sec. 3.2.1) */
     if (scheme == OR_C4 || scheme == OR_C6) deriv_compact_1d(scheme, n, periodic, f, df);
     else deriv_explicit_1d(scheme, n, periodic, f, df);
 }
@@ -543,7 +544,7 @@ or_ctx* or_create(const or_grid_desc* desc, const double* xyz, int scheme,
         int plo = desc->bc_lo[d] == OR_BC_PERIODIC, phi = desc->bc_hi[d] == OR_BC_PERIODIC;
         if (plo != phi) return NULL;
     }
-    if (scheme < OR_E2 || scheme > OR_C6) return NULL;
+    if (scheme < OR_E2 || scheme > OR_UW) return NULL;
     or_ctx* C = (or_ctx*)calloc(1, sizeof(or_ctx));
     C->g = *desc;
     C->N = desc->n[0] * desc->n[1] * desc->n[2];
@@ -612,6 +613,150 @@ static void apply_bc(const or_ctx* C, double* phi, int poisson)
 }
 
 void or_apply_bc(const or_ctx* C, double* phi) { apply_bc(C, phi, 0); }
+
+/* ------------------------------------------------------------------------------------ */
+/* baseline upwind scheme (Sec. 3.2.1, Eqs. UW1-UW5) and the level-set equation (Sec. 5.5) */
+/* ------------------------------------------------------------------------------------ */
+
+/* Backward and forward differences B_l, F_l along direction dir at unit computational
+ * spacing (Eq. UW2).  Periodic lines wrap; the end node of an open line has one of the two
+ * and uses it for both (such nodes are wall, far-field or Neumann nodes, whose values the
+ * boundary conditions set). */
+static void one_sided_diffs(const or_ctx* C, int dir, const double* phi, double* B, double* F)
+{
+    const or_grid_desc* g = &C->g;
+    int n = g->n[dir];
+    int per = is_periodic(g, dir);
+    int* ids = (int*)malloc(sizeof(int) * n);
+    int L = line_count(C, dir);
+    for (int q = 0; q < L; q++) {
+        line_nodes(g, dir, q, ids);
+        for (int t = 0; t < n; t++) {
+            double b = 0.0, f = 0.0;
+            int have_b = per || t > 0, have_f = per || t < n - 1;
+            if (have_b) b = phi[ids[t]] - phi[ids[per ? wrap(t - 1, n) : t - 1]];
+            if (have_f) f = phi[ids[per ? wrap(t + 1, n) : t + 1]] - phi[ids[t]];
+            if (!have_b) b = f;
+            if (!have_f) f = b;
+            B[ids[t]] = b;
+            F[ids[t]] = f;
+        }
+    }
+    free(ids);
+}
+
+/* SIGN(1, x) of Eqs. UW4-UW5: +1 for x >= 0, -1 for x < 0 */
+static double sign1(double x) { return x >= 0.0 ? 1.0 : -1.0; }
+
+/* Eqs. UW3-UW5.  The weight n_{i-1} is 1 where B >= 0 and B + F >= 0: phi grows from node
+ * i-1 and that side is upwind, so the slope is the difference that reaches node i-1, B.
+ * The weight n_{i+1} is 1 where F < 0 and B + F < 0, and takes F.  Both weights vanish at a
+ * local minimum of phi (B < 0 < F), where the slope is 0.  (The printed Eq. UW3 pairs
+ * n_{i-1} with F; that pairing takes the downwind difference, so the weights are read as
+ * naming the side their difference reaches.) */
+double or_upwind_slope(double B, double F)
+{
+    double s = sign1(F + B);
+    double n_im1 = 0.25 * (1.0 + s) * (1.0 + sign1(B));
+    double n_ip1 = 0.25 * (1.0 - s) * (1.0 - sign1(F));
+    return n_im1 * B + n_ip1 * F;
+}
+
+/* Eq. UW1 summed over the directions: sum_l Uh_l d(phi)/d(xi_l) with
+ * Uh_l = sum_m d(xi_l)/d(x_m) U_m, U_m = sum_k d(xi_k)/d(x_m) s_k and s_k the upwind slope
+ * along k (Eqs. UW3-UW5); each direction's product takes B where Uh_l >= 0, F where < 0. */
+void or_upwind_advection(const or_ctx* C, const double* phi, double* adv)
+{
+    int N = C->N, nd = C->g.ndim;
+    double* B = (double*)malloc(sizeof(double) * (size_t)3 * N);
+    double* F = (double*)malloc(sizeof(double) * (size_t)3 * N);
+    for (int l = 0; l < nd; l++) one_sided_diffs(C, l, phi, B + (size_t)l * N, F + (size_t)l * N);
+    for (int p = 0; p < N; p++) {
+        double sl[3] = {0.0, 0.0, 0.0}, Um[3] = {0.0, 0.0, 0.0};
+        for (int k = 0; k < nd; k++) sl[k] = or_upwind_slope(B[(size_t)k * N + p], F[(size_t)k * N + p]);
+        for (int m = 0; m < nd; m++)
+            for (int k = 0; k < nd; k++) Um[m] += C->xi[(k * 3 + m) * N + p] * sl[k];
+        double a = 0.0;
+        for (int l = 0; l < nd; l++) {
+            double uh = 0.0;
+            for (int m = 0; m < nd; m++) uh += C->xi[(l * 3 + m) * N + p] * Um[m];
+            a += 0.5 * (uh + fabs(uh)) * B[(size_t)l * N + p] + 0.5 * (uh - fabs(uh)) * F[(size_t)l * N + p];
+        }
+        adv[p] = a;
+    }
+    free(B);
+    free(F);
+}
+
+/* |grad phi| = (sum_m U_m^2)^(1/2) with U_m from the upwind slopes.  For F < 0 the front
+ * moves towards decreasing phi: the slopes are those of -phi (differences -B, -F), whose
+ * magnitude is what enters |grad phi|. */
+void or_levelset_gradmag(const or_ctx* C, double Fs, const double* phi, double* gm)
+{
+    int N = C->N, nd = C->g.ndim;
+    double sg = Fs < 0.0 ? -1.0 : 1.0;
+    double* B = (double*)malloc(sizeof(double) * (size_t)3 * N);
+    double* F = (double*)malloc(sizeof(double) * (size_t)3 * N);
+    for (int l = 0; l < nd; l++) one_sided_diffs(C, l, phi, B + (size_t)l * N, F + (size_t)l * N);
+    for (int p = 0; p < N; p++) {
+        double sl[3] = {0.0, 0.0, 0.0}, g2 = 0.0;
+        for (int k = 0; k < nd; k++)
+            sl[k] = or_upwind_slope(sg * B[(size_t)k * N + p], sg * F[(size_t)k * N + p]);
+        for (int m = 0; m < nd; m++) {
+            double u = 0.0;
+            for (int k = 0; k < nd; k++) u += C->xi[(k * 3 + m) * N + p] * sl[k];
+            g2 += u * u;
+        }
+        gm[p] = sqrt(g2);
+    }
+    free(B);
+    free(F);
+}
+
+/* zero normal gradient on every non-periodic face (Sec. 5.5), direction by direction */
+static void levelset_bc(const or_ctx* C, double* phi)
+{
+    const or_grid_desc* g = &C->g;
+    for (int d = 0; d < g->ndim; d++) {
+        if (is_periodic(g, d)) continue;
+        int stride = d == 0 ? 1 : (d == 1 ? g->n[0] : g->n[0] * g->n[1]);
+        for (int side = 0; side < 2; side++) {
+            int s = side ? -stride : stride;
+            for (int p = 0; p < C->N; p++)
+                if (on_face(g, p, d, side)) phi[p] = phi[p + s];
+        }
+    }
+}
+
+void or_levelset_steps(const or_ctx* C, double Fs, double dt, double* phi, int n)
+{
+    int N = C->N;
+    double* p0 = (double*)malloc(sizeof(double) * N);
+    double* s = (double*)malloc(sizeof(double) * N);
+    double* gm = (double*)malloc(sizeof(double) * N);
+    double* K[4];
+    for (int k = 0; k < 4; k++) K[k] = (double*)malloc(sizeof(double) * N);
+    static const double cst[4] = {0.0, 0.5, 0.5, 1.0};
+    for (int it = 0; it < n; it++) {
+        memcpy(p0, phi, sizeof(double) * N);
+        for (int k = 0; k < 4; k++) {
+            if (k == 0) memcpy(s, p0, sizeof(double) * N);
+            else {
+                for (int p = 0; p < N; p++) s[p] = p0[p] + cst[k] * dt * K[k - 1][p];
+                levelset_bc(C, s);
+            }
+            or_levelset_gradmag(C, Fs, s, gm);
+            for (int p = 0; p < N; p++) K[k][p] = -Fs * gm[p];       /* Eq. levelset, RHS 0 */
+        }
+        for (int p = 0; p < N; p++)
+            phi[p] = p0[p] + dt / 6.0 * (K[0][p] + 2.0 * K[1][p] + 2.0 * K[2][p] + K[3][p]);
+        levelset_bc(C, phi);
+    }
+    free(p0);
+    free(s);
+    free(gm);
+    for (int k = 0; k < 4; k++) free(K[k]);
+}
 
 /* ------------------------------------------------------------------------------------ */
 /* right-hand sides                                                                     */
@@ -689,6 +834,13 @@ void or_rhs_hj(const or_ctx* C, const or_params* P, const double* phi, double* R
     grad_phys(C, P->scheme, phi, U);
     div_phys(C, P->scheme, U, lap);
 
+    /* baseline scheme: the advection term U.grad(phi) by upwinding (Eqs. UW1-UW5) */
+    double* adv = NULL;
+    if (P->scheme == OR_UW) {
+        adv = (double*)malloc(sizeof(double) * N);
+        or_upwind_advection(C, phi, adv);
+    }
+
     /* Nakanishi curvature (Eq. 25): kappa = div(n), n = grad(phi) / (|grad(phi)| + eps0) */
     if (P->curvature) {
         double* nv = (double*)calloc((size_t)3 * N, sizeof(double));
@@ -734,12 +886,13 @@ void or_rhs_hj(const or_ctx* C, const or_params* P, const double* phi, double* R
             gam = a < b ? a : b;
         } else gam = 0.0;                                                  /* Eq. 17 */
         double v = 0.0, r;
+        double a2 = adv ? adv[p] : g2;                                     /* U.grad(phi) */
         if (P->curvature) {
             v = 0.001 * (1.0 - gm) * (1.0 - gm);
             double corr = gm * kap[p] > 0.0 ? gm * kap[p] : 0.0;
-            r = 1.0 + (gam + v) * (lap[p] - corr) - g2;                    /* Eq. 25 */
+            r = 1.0 + (gam + v) * (lap[p] - corr) - a2;                    /* Eq. 25 */
         } else {
-            r = 1.0 + gam * lap[p] - g2;                                   /* Eqs. 5, 18 */
+            r = 1.0 + gam * lap[p] - a2;                                   /* Eqs. 5, 18 */
         }
         R[p] = r;
         if (dt) {
@@ -752,6 +905,7 @@ void or_rhs_hj(const or_ctx* C, const or_params* P, const double* phi, double* R
     free(kap);
     free(lad);
     free(d4);
+    free(adv);
 }
 
 void or_rhs_poisson(const or_ctx* C, const or_params* P, const double* phi, double* R, double* dt)

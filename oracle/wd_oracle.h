@@ -35,6 +35,8 @@ extern "C" {
 #define OR_E6 2
 #define OR_C4 3
 #define OR_C6 4
+#define OR_UW 5   /* baseline: upwind advection term (Eqs. UW1-UW5), E2 for the metrics
+                     and the Laplacian (Sec. 3.2.1) */
 
 /* equations */
 #define OR_HJ_STD  0   /* Gamma = eps*phi, Eq. 6 */
@@ -127,6 +129,23 @@ void or_poisson_steps(const or_ctx* c, const or_params* p, double* phip, int n, 
 /* Full solve: initial guess, HJ pseudo-time marching to the tolerance. Returns 0 when
  * converged, 1 when max_iters was reached, 2 on divergence. */
 int or_solve(const or_ctx* c, const or_params* p, double* phi, or_stats* st);
+
+/* Advection term of the baseline upwind scheme (Sec. 3.2.1, Eqs. UW1-UW5):
+ * adv = sum_l [0.5 (Uh_l + |Uh_l|) B_l + 0.5 (Uh_l - |Uh_l|) F_l] with Uh_l the contravariant
+ * component of grad(phi) built from the upwind slopes. */
+void or_upwind_advection(const or_ctx* c, const double* phi, double* adv);
+
+/* Upwind slope of Eqs. UW3-UW5 from the backward and forward differences B and F. */
+double or_upwind_slope(double B, double F);
+
+/* |grad phi| of the level-set equation (Eq. levelset) from the upwind slopes, for a front
+ * moving at normal speed F (the selection is mirrored for F < 0). */
+void or_levelset_gradmag(const or_ctx* c, double F, const double* phi, double* gm);
+
+/* n steps of the level-set equation d(phi)/dt + F |grad phi| = 0 (Sec. 5.5) by classical RK4
+ * with the global time step dt; zero normal gradient on every non-periodic face after each
+ * stage.  Dirichlet nodes are not held. */
+void or_levelset_steps(const or_ctx* c, double F, double dt, double* phi, int n);
 
 /* Dense-free tridiagonal helpers exported for pinning: rows a_i x_{i-1} + b_i x_i +
  * c_i x_{i+1} = d_i.  cyclic != 0 couples a_0 to x_{n-1} and c_{n-1} to x_0. */
