@@ -339,6 +339,8 @@ def run_native(args, rank, world):
             d["frac_of_fused_roofline"] = round(d["mcell_iter_s"] * 1e6 * 112 / (peak_hbm_gbs * 1e9), 4)
             out["duct"] = d
             out["square65"] = square_report(wd)
+            out["upwind_vs_central"] = upwind_report(wd)
+            out["levelset_regression"] = levelset_report(wd)
         out["cpu_baseline"] = cpu_baseline()
         print(json.dumps(out), flush=True)
     if world > 1:
@@ -439,6 +441,128 @@ def star_report(wd, full):
             "warm_iters_median": int(np.median(its)), "total_s": round(total, 2),
             "perimeter": round(L, 5), "perimeter_exact_field": round(Lx, 5),
             "perimeter_rel_err": round((L - Lx) / Lx, 5), "max_err_near_port_h": round(err / h, 3)}
+
+
+def _ms_per_steps(wd, g, p, phi, n):
+    import torch
+
+    g.steps(p, phi, 3)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record()
+    g.steps(p, phi, n)
+    ev1.record()
+    torch.cuda.synchronize()
+    return ev0.elapsed_time(ev1)
+
+
+def upwind_report(wd):
+    """The baseline upwind scheme (UW, Sec. 3.2.1) against the central schemes, as in the
+    paper's timing comparison (time per 100 pseudo steps on the channel): channel 1024 x 513
+    nodes, FP64.  For UW with the standard HJ, E2 and E4 with the standard HJ, E4 and C6 with
+    LAD: ms per 100 pseudo steps on the generic per-operator path (the only path of UW) and
+    on the scheme's own fast path, pseudo steps to converge (tol_l2 1e-10) and the max error
+    against the exact distance min(y, 1 - y)."""
+    import os
+
+    import numpy as np
+    import torch
+
+    from paper_2111_09859_gb300 import workloads as W
+
+    sp = W.channel(1024, 513)
+    y = sp.xyz[1]
+    ex = np.minimum(y, 1.0 - y)
+    cases = [("UW_std", wd.UW, wd.HJ_STD), ("E2_std", wd.E2, wd.HJ_STD), ("E4_std", wd.E4, wd.HJ_STD),
+             ("E4_lad", wd.E4, wd.HJ_LAD), ("C6_lad", wd.C6, wd.HJ_LAD)]
+    out = {"grid": "channel 1024 x 513 (periodic x, walls y = 0, 1), FP64"}
+    for name, sch, eq in cases:
+        p = wd.default_params(sch, equation=eq, tol_l2=1e-10, max_iters=40000)
+        row = {}
+        for path in ("generic", "fast"):
+            if path == "fast" and sch == wd.UW:
+                continue
+            if path == "generic":
+                os.environ["WD_FORCE_GENERIC"] = "1"
+            try:
+                g = wd.Grid(sp, wd.FP64, sch)
+            finally:
+                os.environ.pop("WD_FORCE_GENERIC", None)
+            phi = g.as_field(ex)
+            row["ms_per_100_steps_" + path] = round(_ms_per_steps(wd, g, p, phi, 100), 3)
+            if path == "generic":
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                sol, st = g.solve(p)
+                torch.cuda.synchronize()
+                row["solve_s"] = round(time.perf_counter() - t0, 3)
+                row["iters"] = st["iters"]
+                row["max_err_vs_exact"] = float(np.abs(sol.double().cpu().numpy() - ex).max())
+            g.close()
+        out[name] = row
+    uw = out["UW_std"]["ms_per_100_steps_generic"]
+    out["uw_time_over"] = {k: round(uw / out[k]["ms_per_100_steps_generic"], 3)
+                           for k in ("E2_std", "E4_std", "E4_lad", "C6_lad")}
+    out["uw_time_over_fast_path"] = {k: round(uw / out[k]["ms_per_100_steps_fast"], 3)
+                                     for k in ("E2_std", "E4_std", "E4_lad", "C6_lad")}
+    return out
+
+
+def levelset_report(wd):
+    """Grain regression (Sec. 5.5): the 1025^2 star, FP32.  The HJ-LAD field of the star (its
+    first solve) starts the level-set march d(phi)/dt + F |grad phi| = 0 at F = 0.3 to t = 1
+    (RK4, dt = 0.5 h / F, upwind slopes of Eqs. UW3-UW5).  Reports ms per step, node updates
+    per second, the stage kernel's algorithmic HBM bytes and its fraction of the measured
+    copy bandwidth, and the burning perimeter at t = 0.25 .. 1 against the exact front
+    {d_0 = F t} (marching squares on the exact field); the same march started from the exact
+    d_0 separates the march's own error from the initialization's."""
+    import numpy as np
+    import torch
+
+    from paper_2111_09859_gb300 import workloads as W
+
+    sp = W.star(1025)
+    h, d0 = sp.meta["h"], sp.meta["signed_distance"]
+    g = wd.Grid(sp, wd.FP32_METRIC64, wd.E4)
+    p = wd.default_params(wd.E4, equation=wd.HJ_LAD, eps=0.15, alpha_f=0.45, lad_exp=4.0, tol_l2=1e-6,
+                          max_iters=20000)
+    phi, st = g.solve(p)
+    F, T, parts = 0.3, 1.0, 4
+    ns_ = int(np.ceil(T / (0.5 * h / F) / parts)) * parts
+    exm = g.as_field(d0)
+    g.levelset(exm, F, T / ns_, ns_)
+    L_exact_start = g.level_length(exm, 0.0)
+    ns = int(np.ceil(T / (0.5 * h / F) / parts)) * parts
+    dt = T / ns
+    g.levelset(phi.clone(), F, dt, 4)                        # warm-up: graph capture
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(parts + 1)]
+    per = []
+    torch.cuda.synchronize()
+    ms = 0.0
+    for k in range(parts):
+        ev[k].record()
+        g.levelset(phi, F, dt, ns // parts)
+        ev[k + 1].record()
+        torch.cuda.synchronize()
+        ms += ev[k].elapsed_time(ev[k + 1])
+        t = (k + 1) * T / parts
+        L = g.level_length(phi, 0.0)
+        Lx = g.level_length(g.as_field(d0), F * t)
+        per.append({"t": t, "perimeter": round(L, 5), "exact": round(Lx, 5), "rel_err": round(L / Lx - 1, 5)})
+    nodes = sp.N
+    ms_step = ms / ns
+    # per stage: src, phin and dst once, acc read-modify-write on two stages, 4 metric arrays
+    bytes_stage = nodes * (4 * 4.5 + 4 * 4)
+    stage_us = ms_step * 1e3 / 4
+    g.close()
+    return {"grid": "1025x1025 on [-1,1]^2", "F": F, "t_end": T, "steps": ns, "dt": dt,
+            "init_iters": st["iters"], "ms_per_step": round(ms_step, 4),
+            "mnode_steps_per_s": round(nodes / (ms_step * 1e-3) / 1e6, 1),
+            "stage_algorithmic_bytes": int(bytes_stage),
+            "stage_hbm_frac_of_measured": round(bytes_stage / (stage_us * 1e-6) / (peak_hbm()[0] * 1e9), 4),
+            "perimeter": per,
+            "perimeter_from_exact_d0_at_t_end": {"value": round(L_exact_start, 5),
+                                                 "rel_err": round(L_exact_start / per[-1]["exact"] - 1, 5)}}
 
 
 def duct_report(wd):

@@ -70,7 +70,12 @@ enum { WD_HJ_STD = 0,        /* Gamma = eps * phi (Eq. 6) */
        WD_EIKONAL = 2 };     /* Gamma = 0 (Eq. 17) */
 
 /* spatial scheme (Sec. 3.2.2, Eq. 16) */
-enum { WD_E2 = 0, WD_E4 = 1, WD_E6 = 2, WD_C4 = 3, WD_C6 = 4 };
+enum { WD_E2 = 0, WD_E4 = 1, WD_E6 = 2, WD_C4 = 3, WD_C6 = 4,
+       WD_UW = 5 };          /* the paper's baseline (Sec. 3.2.1): the advection term U.grad(phi)
+                                of the HJ / Eikonal equations by first-order upwinding with the
+                                sign-selected slopes of Eqs. UW1-UW5; the metrics, the Laplacian
+                                and the Poisson guess by E2.  Runs on the generic per-operator
+                                path; wd_default_params turns the filter off for it. */
 
 /* initial guess */
 enum { WD_INIT_ZERO = 0,     /* phi = 0 (Sec. 3.5) */
@@ -86,7 +91,8 @@ typedef struct {
     int bc_hi[3];          /* WD_BC_* of the face at index n-1 of each direction */
     double period[3][3];   /* periodic direction d: x(i + n[d]) = x(i) + period[d] */
     int precision;         /* WD_FP64 / WD_FP32_METRIC64 / WD_FP32 */
-    int scheme;            /* WD_E2 .. WD_C6: every derivative and the metrics (Sec. 3.2.2) */
+    int scheme;            /* WD_E2 .. WD_C6: every derivative and the metrics (Sec. 3.2.2);
+                              WD_UW: the baseline upwind scheme */
     double L_ref;          /* reference length of the convergence norms (Eq. 20) */
 } wd_grid_desc;
 
@@ -279,6 +285,18 @@ wd_status wd_reset_geometry(wd_grid g, const double* xyz_host, const uint8_t* ma
  * Errors: WD_ERR_INVALID_ARG for NULL arrays, s < 0 or floor > 0. */
 wd_status wd_recede(wd_grid g, void* phi_dev, double s, double floor, uint8_t* mask_dev,
                     void* dval_dev);
+
+/* Grain regression (Sec. 5.5, Eq. levelset with right-hand side 0): nsteps steps of
+ * d(phi)/dt + F |grad phi| = 0 by classical RK4 with the global time step dt, on the dense
+ * field phi_dev (n[0]*n[1]*n[2] values of the grid's state precision, updated in place; 2-D,
+ * stacked 2-D or 3-D).  |grad phi| = |sum_l grad(xi_l) s_l| with s_l the upwind slopes of
+ * Eqs. UW3-UW5 (of -phi when F < 0, so that the front always takes its upwind side); the
+ * front {phi = 0} moves along grad(phi) at speed F.  Every non-periodic face holds a zero
+ * normal gradient (the face node copies its neighbour after every stage); Dirichlet nodes
+ * and the grid's wall faces are not held.  Stable for dt * |F| * sum_l |grad xi_l| below about
+ * 1.4 (RK4 on first-order upwinding); the caller picks dt.  Synchronous.
+ * Errors: WD_ERR_INVALID_ARG for NULL phi_dev, nsteps < 0, dt <= 0 or non-finite F / dt. */
+wd_status wd_levelset(wd_grid g, void* phi_dev, double F, double dt, int nsteps);
 
 /* Length of the level set {phi = level} of a single 2-D grid (the burning perimeter when
  * phi is the wall distance and level = 0 or the burned depth): marching squares over every

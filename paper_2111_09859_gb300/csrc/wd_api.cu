@@ -47,8 +47,12 @@ wd_status cuda_error(cudaError_t e, const char* where)
 
 enum {
     W_PHIN, W_PHIS, W_ACC, W_DT, W_D0, W_D1, W_D2, W_U0, W_U1, W_U2, W_N0, W_N1, W_N2,
-    W_LAP, W_KAP, W_LAD, W_T0, W_T1, W_NWORK
+    W_LAP, W_KAP, W_LAD, W_T0, W_T1, W_ADV, W_NWORK
 };
+
+// the baseline upwind scheme takes its central terms (metrics, Laplacian, Poisson guess)
+// from E2 (Sec. 3.2.1)
+static inline int central_scheme(int s) { return s == WD_UW ? WD_E2 : s; }
 
 struct wd_grid_s {
     Dims D;
@@ -99,6 +103,10 @@ struct wd_grid_s {
     int gx_n[2] = {0, 0};
     unsigned gx_gen[2] = {0, 0};
     wd_solve_params gx_p[2];
+    // CUDA graph of two level-set steps, reused while F, dt and the geometry are unchanged
+    cudaGraphExec_t lsx = nullptr;
+    double ls_F = 0.0, ls_dt = 0.0;
+    unsigned ls_gen = 0;
     // kernel timer (wd_profile)
     int prof_on = 0;
     std::vector<cudaEvent_t> ev_pool;
@@ -219,7 +227,7 @@ static wd_status validate_desc(const wd_grid_desc* d)
             return set_error(WD_ERR_INVALID_ARG, "periodic must be set on both faces");
     }
     if (d->precision < 0 || d->precision > 2) return set_error(WD_ERR_INVALID_ARG, "bad precision");
-    if (d->scheme < WD_E2 || d->scheme > WD_C6) return set_error(WD_ERR_INVALID_ARG, "bad scheme");
+    if (d->scheme < WD_E2 || d->scheme > WD_UW) return set_error(WD_ERR_INVALID_ARG, "bad scheme");
     if (!(d->L_ref > 0.0)) return set_error(WD_ERR_INVALID_ARG, "L_ref must be positive");
     long long tot = (long long)((d->n[0] + 31) / 32 * 32) * d->n[1] * d->n[2];
     if (tot > (1LL << 31)) return set_error(WD_ERR_INVALID_ARG, "grid too large");
@@ -280,6 +288,7 @@ static void release(wd_grid g)
     for (auto& e : g->ev_pool) cudaEventDestroy(e);
     for (int k = 0; k < 2; k++)
         if (g->gx[k]) cudaGraphExecDestroy(g->gx[k]);
+    if (g->lsx) cudaGraphExecDestroy(g->lsx);
     if (g->ev_in) cudaEventDestroy(g->ev_in);
     if (g->ev_out) cudaEventDestroy(g->ev_out);
     if (g->stream) cudaStreamDestroy(g->stream);
@@ -390,7 +399,7 @@ struct Solver {
         LineOp op;
         std::memset(&op, 0, sizeof(op));
         op.kind = OPK_DERIV;
-        op.scheme = g->desc.scheme;
+        op.scheme = central_scheme(g->desc.scheme);
         return op;
     }
     static wd_status op_filter(double al, LineOp& op)
@@ -542,6 +551,7 @@ struct Solver {
         a.lap = W(W_LAP);
         a.kap = W(W_KAP);
         a.lad = lad;
+        a.adv = nullptr;
         a.sig1 = (const M*)g->sig1;
         a.sig2 = (const M*)g->sig2;
         a.eps = p->eps;
@@ -561,6 +571,10 @@ struct Solver {
         if (!poisson && p->equation == WD_HJ_LAD) ST(lad_part(src, &lad));
         StageArgs<T, M> a = stage_args(src, dst, poisson, lad);
         ProfScope ps(g, WD_K_POINT);
+        if (!poisson && g->desc.scheme == WD_UW) {
+            CK(launch_uw_adv<T, M>(D, src, xi(), W(W_ADV), st));
+            a.adv = W(W_ADV);
+        }
         CK(launch_stage<T, M>(D, a, stage, st));
         return WD_OK;
     }
@@ -569,7 +583,7 @@ struct Solver {
     // along direction-1 lines), see wd_fused2d.cu
     bool fused2d() const
     {
-        if (D.ndim != 2 || g->force_generic) return false;
+        if (D.ndim != 2 || g->force_generic || g->desc.scheme == WD_UW) return false;
         auto ok = [](int k) { return k == WD_BC_PERIODIC || k == WD_BC_WALL; };
         return ok(g->desc.bc_lo[0]) && ok(g->desc.bc_hi[0]);
     }
@@ -730,7 +744,7 @@ struct Solver {
     {
         if (!g->cart || g->force_generic || g->batch != 1) return false;
         const int sch = g->desc.scheme;
-        if (sch == WD_C4 || sch == WD_C6) return false;
+        if (sch == WD_C4 || sch == WD_C6 || sch == WD_UW) return false;
         if (D.ndim == 2) return true;
         for (int d = 0; d < 3; d++)
             for (int k : {g->desc.bc_lo[d], g->desc.bc_hi[d]})
@@ -1178,6 +1192,78 @@ struct Solver {
         return WD_OK;
     }
 
+    // one step of the level-set equation (Sec. 5.5) from a to b: four stage kernels whose
+    // outputs never alias their inputs (a -> T0 -> T1 -> T0 -> b, phin = a)
+    wd_status ls_step(T* a, T* b, double F, double dt)
+    {
+        LsArgs<T, M> x;
+        x.phin = a;
+        x.acc = W(W_ACC);
+        x.xi = xi();
+        x.F = F;
+        x.dt = dt;
+        T* io[5] = {a, W(W_T0), W(W_T1), W(W_T0), b};
+        for (int k = 0; k < 4; k++) {
+            x.src = io[k];
+            x.dst = io[k + 1];
+            ProfScope ps(g, WD_K_POINT);
+            CK(launch_ls_stage<T, M>(D, x, k, st));
+        }
+        return WD_OK;
+    }
+
+    // n level-set steps; the state alternates between W_PHIN and W_PHIS.  Pairs of steps
+    // (PHIN -> PHIS -> PHIN) run as one CUDA graph, captured after a first uncaptured pair
+    // and kept with the grid for the same F and dt.
+    wd_status levelset(void* phi_user, double F, double dt, int n)
+    {
+        CK(to_padded(g, W(W_PHIN), phi_user, sizeof(T)));
+        T* a = W(W_PHIN);
+        T* b = W(W_PHIS);
+        int pairs = n / 2;
+        const bool hit = g->lsx && g->ls_F == F && g->ls_dt == dt && g->ls_gen == g->gen;
+        if (pairs > 0 && (g->prof_on || !hit)) {
+            ST(ls_step(a, b, F, dt));
+            ST(ls_step(b, a, F, dt));
+            pairs--;
+            if (g->prof_on) {
+                for (; pairs > 0; pairs--) {
+                    ST(ls_step(a, b, F, dt));
+                    ST(ls_step(b, a, F, dt));
+                }
+            } else if (pairs > 0) {
+                if (g->lsx) cudaGraphExecDestroy(g->lsx);
+                g->lsx = nullptr;
+                cudaGraph_t graph = nullptr;
+                CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+                wd_status rs = ls_step(a, b, F, dt);
+                if (rs == WD_OK) rs = ls_step(b, a, F, dt);
+                cudaError_t ce = cudaStreamEndCapture(st, &graph);
+                if (rs != WD_OK) {
+                    if (graph) cudaGraphDestroy(graph);
+                    return rs;
+                }
+                CK(ce);
+                cudaGraphExec_t ex = nullptr;
+                ce = cudaGraphInstantiate(&ex, graph, 0);
+                cudaGraphDestroy(graph);
+                CK(ce);
+                g->lsx = ex;
+                g->ls_F = F;
+                g->ls_dt = dt;
+                g->ls_gen = g->gen;
+            }
+        }
+        for (; pairs > 0; pairs--) CK(cudaGraphLaunch(g->lsx, st));
+        if (n % 2) {
+            ST(ls_step(a, b, F, dt));
+            std::swap(a, b);
+        }
+        CK(from_padded(g, phi_user, a, sizeof(T)));
+        CK(cudaStreamSynchronize(st));
+        return WD_OK;
+    }
+
     wd_status rhs(int kind, const void* phi_user, void* R_user, void* dt_user)
     {
         bool poisson = kind == 1;
@@ -1218,7 +1304,7 @@ static wd_status alloc_impl(wd_grid g)
     for (int d = 0; d < D.ndim; d++) {
         std::vector<double> a, c;
         int imp;
-        derivative_rows(g->desc.scheme, D.n[d], D.per[d], a, c, imp);
+        derivative_rows(central_scheme(g->desc.scheme), D.n[d], D.per[d], a, c, imp);
         ST(build_line_table(D.n[d], D.per[d], a, c, imp, g->dtab[d]));
         std::vector<double> z(D.n[d], 0.0);
         ST(build_line_table(D.n[d], D.per[d], z, z, 0, g->etab[d]));
@@ -1354,7 +1440,7 @@ static wd_status geometry_impl(wd_grid g, const double* xyz_host, const uint8_t*
         LineOp op;
         std::memset(&op, 0, sizeof(op));
         op.kind = OPK_DERIV;
-        op.scheme = g->desc.scheme;
+        op.scheme = central_scheme(g->desc.scheme);
         for (int l = 0; l < D.ndim && ce == cudaSuccess; l++)
             for (int m = 0; m < D.ndim && ce == cudaSuccess; m++) {
                 double shift = D.per[l] ? g->desc.period[l][m] : 0.0;
@@ -1461,7 +1547,7 @@ void wd_default_params(int scheme, wd_solve_params* p)
     p->C_lad = 0.1;
     p->lad_exp = 3.0;
     p->alpha_f = 0.49;
-    p->filter = 1;
+    p->filter = scheme == WD_UW ? 0 : 1;     // the baseline's upwinding damps by itself
     p->cfl = (scheme == WD_C4 || scheme == WD_C6) ? 0.6 : 0.8;
     p->eps0 = 1e-8;
     p->tol_l2 = 1e-10;
@@ -1754,6 +1840,19 @@ wd_status wd_recede(wd_grid g, void* phi_dev, double s, double floor, uint8_t* m
         using T = std::remove_pointer_t<decltype(t)>;
         CK(launch_recede<T>((T*)phi_dev, n, s, floor, mask_dev, (T*)dval_dev, g->stream));
         return WD_OK;
+    });
+}
+
+wd_status wd_levelset(wd_grid g, void* phi_dev, double F, double dt, int nsteps)
+{
+    if (!g || !phi_dev || nsteps < 0 || !std::isfinite(F) || !(dt > 0.0) || !std::isfinite(dt))
+        return set_error(WD_ERR_INVALID_ARG, "bad level-set arguments");
+    StreamGuard sg(g);
+    return dispatch(g, [&](auto* t, auto* m) {
+        using T = std::remove_pointer_t<decltype(t)>;
+        using M = std::remove_pointer_t<decltype(m)>;
+        Solver<T, M> S(g, nullptr);
+        return S.levelset(phi_dev, F, dt, nsteps);
     });
 }
 

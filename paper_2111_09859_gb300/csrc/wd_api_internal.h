@@ -35,6 +35,7 @@ struct StageArgs {
     const T* lap;        // div(U)
     const T* kap;        // div(n) (curvature only)
     const T* lad;        // smoothed C|LAD| (LAD only)
+    const T* adv;        // upwind U.grad(phi) (baseline scheme only; else |U|^2 is used)
     const M* sig1;       // sum_l |grad xi_l|
     const M* sig2;       // sum_l |grad xi_l|^2
     double eps, cfl;
@@ -73,6 +74,23 @@ cudaError_t launch_norms(const Dims& D, const T* newp, T* oldp, const uint8_t* m
                          cudaStream_t st);
 template <typename T>
 cudaError_t launch_fill(T* p, long long n, T v, cudaStream_t st);
+
+// baseline upwind advection term (wd_upwind.cu)
+template <typename T, typename M>
+cudaError_t launch_uw_adv(const Dims& D, const T* phi, const M* xi, T* adv, cudaStream_t st);
+
+// one RK4 stage of the level-set equation (wd_upwind.cu)
+template <typename T, typename M>
+struct LsArgs {
+    const T* src;        // phi at which the stage evaluates F |grad phi|
+    T* dst;              // stage output (aliases neither src nor phin)
+    const T* phin;       // phi at the start of the step
+    T* acc;              // running sum of the RK4 weights times the right-hand side
+    const M* xi;         // 9 metric arrays d(xi_l)/d(x_m) at (l*3+m)
+    double F, dt;        // normal speed, time step
+};
+template <typename T, typename M>
+cudaError_t launch_ls_stage(const Dims& D, const LsArgs<T, M>& a, int stage, cudaStream_t st);
 
 template <typename T>
 cudaError_t launch_recede(T* phi, long long n, double s, double floor, uint8_t* mask, T* dval,

@@ -280,13 +280,14 @@ __global__ void k_stage(Dims D, StageArgs<T, M> a, int stage)
                 T g1 = T(a.eps) * php, g2l = a.lad[e];
                 gam = g1 < g2l ? g1 : g2l;
             }
+            const T a2 = a.adv ? a.adv[e] : g2;                       // U.grad(phi)
             if (a.curvature) {                                         // Eq. 25
                 v = T(0.001) * (T(1) - gm) * (T(1) - gm);
                 T corr = gm * a.kap[e];
                 corr = corr > T(0) ? corr : T(0);
-                R = T(1) + (gam + v) * (a.lap[e] - corr) - g2;
+                R = T(1) + (gam + v) * (a.lap[e] - corr) - a2;
             } else {
-                R = T(1) + gam * a.lap[e] - g2;                        // Eqs. 5, 18
+                R = T(1) + gam * a.lap[e] - a2;                        // Eqs. 5, 18
             }
         }
         if (stage <= 0) {

@@ -20,7 +20,7 @@ OK, ERR_INVALID_ARG, ERR_OOM, ERR_CUDA, ERR_NOT_CONVERGED, ERR_DIVERGED, ERR_TIM
 BC_WALL, BC_FARFIELD, BC_NEUMANN, BC_PERIODIC = 0, 1, 2, 3
 FP64, FP32_METRIC64, FP32 = 0, 1, 2
 HJ_STD, HJ_LAD, EIKONAL = 0, 1, 2
-E2, E4, E6, C4, C6 = 0, 1, 2, 3, 4
+E2, E4, E6, C4, C6, UW = 0, 1, 2, 3, 4, 5
 INIT_ZERO, INIT_POISSON, INIT_GIVEN = 0, 1, 2
 
 
@@ -93,6 +93,7 @@ SIGNATURES = {
     "wd_get_tuning": (_i, [_vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "wd_recede": (_i, [_vp, _vp, _d, _d, _vp, _vp]),
     "wd_level_length": (_i, [_vp, _vp, _d, C.POINTER(C.c_double)]),
+    "wd_levelset": (_i, [_vp, _vp, _d, _d, _i]),
     "wd_server_create": (_i, [C.POINTER(ServerConfig), C.POINTER(_vp)]),
     "wd_server_submit": (_i, [_vp, C.POINTER(GridDesc), _vp, _vp, _vp, C.POINTER(SolveParams), _vp,
                               C.POINTER(C.c_longlong)]),
@@ -246,6 +247,14 @@ class Grid:
         self._sync_stream()
         _check(lib().wd_recede(self._h, _ptr(phi), float(s), float(floor), _ptr(mask), _ptr(dval)))
         return mask, dval
+
+    def levelset(self, phi, F, dt, nsteps):
+        """nsteps RK4 steps of d(phi)/dt + F |grad phi| = 0 (Sec. 5.5) on ``phi`` in place."""
+        if phi.numel() != self.N or phi.dtype != self.dtype or not phi.is_contiguous():
+            raise ValueError("levelset needs a contiguous field of the grid's size and dtype")
+        self._sync_stream()
+        _check(lib().wd_levelset(self._h, _ptr(phi), float(F), float(dt), int(nsteps)))
+        return phi
 
     def level_length(self, phi, level=0.0):
         out = C.c_double()
