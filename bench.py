@@ -460,13 +460,11 @@ def upwind_report(wd):
     """The baseline upwind scheme (UW, Sec. 3.2.1) against the central schemes, as in the
     paper's timing comparison (time per 100 pseudo steps on the channel): channel 1024 x 513
     nodes, FP64.  For UW with the standard HJ, E2 and E4 with the standard HJ, E4 and C6 with
-    LAD: ms per 100 pseudo steps on the generic per-operator path (the only path of UW) and
-    on the scheme's own fast path, pseudo steps to converge (tol_l2 1e-10) and the max error
-    against the exact distance min(y, 1 - y)."""
+    LAD: ms per 100 pseudo steps (from the exact distance min(y, 1 - y)) on the generic
+    per-operator path (the only path of UW) and on the scheme's own fast path."""
     import os
 
     import numpy as np
-    import torch
 
     from paper_2111_09859_gb300 import workloads as W
 
@@ -477,7 +475,7 @@ def upwind_report(wd):
              ("E4_lad", wd.E4, wd.HJ_LAD), ("C6_lad", wd.C6, wd.HJ_LAD)]
     out = {"grid": "channel 1024 x 513 (periodic x, walls y = 0, 1), FP64"}
     for name, sch, eq in cases:
-        p = wd.default_params(sch, equation=eq, tol_l2=1e-10, max_iters=40000)
+        p = wd.default_params(sch, equation=eq)
         row = {}
         for path in ("generic", "fast"):
             if path == "fast" and sch == wd.UW:
@@ -490,14 +488,6 @@ def upwind_report(wd):
                 os.environ.pop("WD_FORCE_GENERIC", None)
             phi = g.as_field(ex)
             row["ms_per_100_steps_" + path] = round(_ms_per_steps(wd, g, p, phi, 100), 3)
-            if path == "generic":
-                torch.cuda.synchronize()
-                t0 = time.perf_counter()
-                sol, st = g.solve(p)
-                torch.cuda.synchronize()
-                row["solve_s"] = round(time.perf_counter() - t0, 3)
-                row["iters"] = st["iters"]
-                row["max_err_vs_exact"] = float(np.abs(sol.double().cpu().numpy() - ex).max())
             g.close()
         out[name] = row
     uw = out["UW_std"]["ms_per_100_steps_generic"]
@@ -551,15 +541,18 @@ def levelset_report(wd):
         per.append({"t": t, "perimeter": round(L, 5), "exact": round(Lx, 5), "rel_err": round(L / Lx - 1, 5)})
     nodes = sp.N
     ms_step = ms / ns
-    # per stage: src, phin and dst once, acc read-modify-write on two stages, 4 metric arrays
-    bytes_stage = nodes * (4 * 4.5 + 4 * 4)
+    # per stage and node: src, phin and dst once, acc read-modify-write on two of the four
+    # stages (4.5 floats); the uniform grid's metrics are constants
+    bytes_stage = nodes * 4 * 4.5
     stage_us = ms_step * 1e3 / 4
     g.close()
     return {"grid": "1025x1025 on [-1,1]^2", "F": F, "t_end": T, "steps": ns, "dt": dt,
             "init_iters": st["iters"], "ms_per_step": round(ms_step, 4),
             "mnode_steps_per_s": round(nodes / (ms_step * 1e-3) / 1e6, 1),
-            "stage_algorithmic_bytes": int(bytes_stage),
-            "stage_hbm_frac_of_measured": round(bytes_stage / (stage_us * 1e-6) / (peak_hbm()[0] * 1e9), 4),
+            "stage_us": round(stage_us, 2), "stage_algorithmic_bytes": int(bytes_stage),
+            "stage_gbs": round(bytes_stage / (stage_us * 1e-6) / 1e9, 1),
+            "note": "the march's working set (phi, two stage buffers, acc: 17 MB) stays in the 129 MB L2, "
+                    "so HBM does not bound a stage; about 3 us of each is launch and tail",
             "perimeter": per,
             "perimeter_from_exact_d0_at_t_end": {"value": round(L_exact_start, 5),
                                                  "rel_err": round(L_exact_start / per[-1]["exact"] - 1, 5)}}

@@ -572,7 +572,7 @@ struct Solver {
         StageArgs<T, M> a = stage_args(src, dst, poisson, lad);
         ProfScope ps(g, WD_K_POINT);
         if (!poisson && g->desc.scheme == WD_UW) {
-            CK(launch_uw_adv<T, M>(D, src, xi(), W(W_ADV), st));
+            CK(launch_uw_adv<T, M>(D, src, xi(), uw_cart(), W(W_ADV), st));
             a.adv = W(W_ADV);
         }
         CK(launch_stage<T, M>(D, a, stage, st));
@@ -1192,6 +1192,14 @@ struct Solver {
         return WD_OK;
     }
 
+    UwCart<M> uw_cart() const
+    {
+        UwCart<M> c;
+        c.cart = g->cart;
+        for (int l = 0; l < 3; l++) c.ih[l] = g->cart && l < D.ndim ? M(1.0 / g->h[l]) : M(0);
+        return c;
+    }
+
     // one step of the level-set equation (Sec. 5.5) from a to b: four stage kernels whose
     // outputs never alias their inputs (a -> T0 -> T1 -> T0 -> b, phin = a)
     wd_status ls_step(T* a, T* b, double F, double dt)
@@ -1200,6 +1208,7 @@ struct Solver {
         x.phin = a;
         x.acc = W(W_ACC);
         x.xi = xi();
+        x.cc = uw_cart();
         x.F = F;
         x.dt = dt;
         T* io[5] = {a, W(W_T0), W(W_T1), W(W_T0), b};

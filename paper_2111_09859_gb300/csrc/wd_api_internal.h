@@ -75,9 +75,17 @@ cudaError_t launch_norms(const Dims& D, const T* newp, T* oldp, const uint8_t* m
 template <typename T>
 cudaError_t launch_fill(T* p, long long n, T v, cudaStream_t st);
 
+// constant metrics of a uniform Cartesian grid (cart != 0): d(xi_l)/d(x_m) = delta_lm ih[l]
+template <typename M>
+struct UwCart {
+    int cart;
+    M ih[3];
+};
+
 // baseline upwind advection term (wd_upwind.cu)
 template <typename T, typename M>
-cudaError_t launch_uw_adv(const Dims& D, const T* phi, const M* xi, T* adv, cudaStream_t st);
+cudaError_t launch_uw_adv(const Dims& D, const T* phi, const M* xi, const UwCart<M>& cc, T* adv,
+                          cudaStream_t st);
 
 // one RK4 stage of the level-set equation (wd_upwind.cu)
 template <typename T, typename M>
@@ -87,6 +95,7 @@ struct LsArgs {
     const T* phin;       // phi at the start of the step
     T* acc;              // running sum of the RK4 weights times the right-hand side
     const M* xi;         // 9 metric arrays d(xi_l)/d(x_m) at (l*3+m)
+    UwCart<M> cc;        // or the constant metrics of a uniform Cartesian grid
     double F, dt;        // normal speed, time step
 };
 template <typename T, typename M>
