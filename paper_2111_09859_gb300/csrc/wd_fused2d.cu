@@ -266,33 +266,32 @@ __device__ __forceinline__ T f2_stage_value(const F2Args<T, M>& a, long long e, 
 template <typename T, typename M>
 __global__ void __launch_bounds__(512) k_f2_stage(F2Args<T, M> a)
 {
+    // one thread per node: i from the x-blocks, j = blockIdx.y, the stacked grid = blockIdx.z
     const Dims& D = a.D;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= D.n[0]) return;
     const int N1 = D.n[1];
+    const int j = blockIdx.y;
     const long long st = D.stride(1);
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < D.total;
-         e += (long long)gridDim.x * blockDim.x) {
-        const int i = (int)(e % D.pitch);
-        if (i >= D.n[0]) continue;
-        const int j = (int)((e / D.pitch) % N1);
-        T out = f2_stage_value(a, e, j, true);
-        const int side = j == 0 ? 0 : (j == N1 - 1 ? 1 : -1);
-        if (side >= 0) {
-            int kind = side ? a.bchi1 : a.bclo1;
-            if (kind == WD_BC_FARFIELD || kind == WD_BC_NEUMANN) {
-                if (a.poisson) kind = WD_BC_NEUMANN;
-                const long long s = side ? -st : st;
-                const T v1 = f2_stage_value(a, e + s, j + (side ? -1 : 1), false);
-                if (kind == WD_BC_NEUMANN) out = v1;
-                else {
-                    const T v2 = f2_stage_value(a, e + 2 * s, j + (side ? -2 : 2), false);
-                    const long long q = e / ((long long)D.pitch * N1);   // stacked grid
-                    out = v1 + T((side ? a.ffr_hi : a.ffr_lo)[q + (long long)D.n[2] * i]) * (v1 - v2);
-                }
+    const long long e = D.idx(i, j, blockIdx.z);
+    T out = f2_stage_value(a, e, j, true);
+    const int side = j == 0 ? 0 : (j == N1 - 1 ? 1 : -1);
+    if (side >= 0) {
+        int kind = side ? a.bchi1 : a.bclo1;
+        if (kind == WD_BC_FARFIELD || kind == WD_BC_NEUMANN) {
+            if (a.poisson) kind = WD_BC_NEUMANN;
+            const long long s = side ? -st : st;
+            const T v1 = f2_stage_value(a, e + s, j + (side ? -1 : 1), false);
+            if (kind == WD_BC_NEUMANN) out = v1;
+            else {
+                const T v2 = f2_stage_value(a, e + 2 * s, j + (side ? -2 : 2), false);
+                const long long q = blockIdx.z;   // stacked grid
+                out = v1 + T((side ? a.ffr_hi : a.ffr_lo)[q + (long long)D.n[2] * i]) * (v1 - v2);
             }
         }
-        if (a.mask[e]) out = a.poisson ? T(0) : a.dval[e];
-        a.dst[e] = out;
     }
+    if (a.mask[e]) out = a.poisson ? T(0) : a.dval[e];
+    a.dst[e] = out;
 }
 
 // ---- F: direction-1 filter, line BCs, change norms and commit ----------------------------
@@ -456,10 +455,11 @@ cudaError_t f2_launch(F2Args<T, M> a, int which, cudaStream_t st)
 {
     const Dims& D = a.D;
     if (which == F2_STAGE) {
-        const int thr = a.stage_threads > 0 ? a.stage_threads : 256;
-        long long b = (D.total + thr - 1) / thr;
-        if (b > 152 * 64) b = 152 * 64;     // about one node per thread
-        k_f2_stage<T, M><<<(int)b, thr, 0, st>>>(a);
+        int thr = a.stage_threads > 0 ? a.stage_threads : 256;
+        const int row = (D.n[0] + 31) / 32 * 32;
+        if (thr > row) thr = row;
+        const dim3 grd((unsigned)((D.n[0] + thr - 1) / thr), (unsigned)D.n[1], (unsigned)D.n[2]);
+        k_f2_stage<T, M><<<grd, thr, 0, st>>>(a);
         return cudaGetLastError();
     }
     const size_t es = sizeof(T);

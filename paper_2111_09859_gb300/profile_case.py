@@ -10,6 +10,9 @@ CASE:
   duct256   square duct 256^3, E6 + LAD, FP32
   duct128   square duct 128 x 128 x 128 (a small case of the same kernels)
   star1025  star port 1025^2, E4 + LAD, FP32
+  star1025-ls  the same star, level-set steps (F = 0.3, dt = 0.5 h / F) instead of pseudo
+            steps, from the exact signed distance
+  chan-uw   channel 1024 x 513, baseline upwind scheme, standard HJ, FP64 (generic path)
   ell2048   one ellipse O-grid 1025 x 2048, C6 + LAD, FP32
 
 The field starts from the exact distance where one exists (random smooth field
@@ -40,7 +43,12 @@ def build_case(name):
         p = wd.default_params(wd.E6, equation=wd.HJ_LAD)
         x, y, z = spec.xyz
         return spec, wd.FP32_METRIC64, wd.E6, p, np.minimum.reduce([y, 1 - y, z, 1 - z])
-    if name == "star1025":
+    if name == "chan-uw":
+        spec = W.channel(1024, 513)
+        p = wd.default_params(wd.UW, equation=wd.HJ_STD)
+        y = spec.xyz[1]
+        return spec, wd.FP64, wd.UW, p, np.minimum(y, 1.0 - y)
+    if name.startswith("star1025"):
         spec = W.star(1025)
         p = wd.default_params(wd.E4, equation=wd.HJ_LAD, eps=0.15, alpha_f=0.45, lad_exp=4.0)
         sd = spec.meta["signed_distance"]
@@ -66,16 +74,27 @@ def main():
     build.build()
     spec, prec, scheme, p, phi0 = build_case(args.case)
     g = wd.Grid(spec, prec, scheme)
-    phi = g.as_field(phi0)
-    g.steps(p, phi, args.warmup)
+    if args.case.endswith("-ls"):
+        phi = g.as_field(spec.meta["signed_distance"])
+        F = 0.3
+        ls_dt = 0.5 * spec.meta["h"] / F
+
+        def run(n):
+            g.levelset(phi, F, ls_dt, n)
+    else:
+        phi = g.as_field(phi0)
+
+        def run(n):
+            g.steps(p, phi, n)
+    run(args.warmup)
     torch.cuda.synchronize()
     if args.timer:
         g.profile(True)
     t = time.time()
-    g.steps(p, phi, args.steps)
+    run(args.steps)
     torch.cuda.synchronize()
     dt = time.time() - t
-    line = f"{args.case}: {spec.N} nodes, {args.steps} pseudo steps, {dt / max(args.steps, 1) * 1e3:.3f} ms/step"
+    line = f"{args.case}: {spec.N} nodes, {args.steps} steps, {dt / max(args.steps, 1) * 1e3:.3f} ms/step"
     if args.timer:
         prof = g.profile_read()
         g.profile(False)

@@ -240,3 +240,67 @@ def test_star_regression_full_size(wd, oracle):
     assert sel.sum() > 1000
     err = np.abs(out[sel] - (phi0[sel] - F * T))
     assert err.max() < 4 * h
+
+
+def _cyl_members(radii):
+    return [W.cylinder(33, 64, 1.1, r_wall=r) for r in radii]
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_uw_stacked_grids(wd, oracle, prec):
+    """Stacked O-grids with the upwind scheme: K pseudo steps of the stack equal K steps of
+    each grid alone, bit for bit, and the oracle's steps of each member."""
+    members = _cyl_members([0.5, 0.4, 0.6])
+    spec = W.stack(members)
+    prm = base_params(wd.UW, equation=1, filter=0)
+    N = members[0].N
+    phi0 = np.concatenate([_init(m, oracle_grid(oracle, m, oracle.UW), 5 + k) for k, m in enumerate(members)])
+    gb = wd.Grid(spec, prec, wd.UW)
+    outb, _ = gb.steps(gpu_params(wd, wd.UW, prm), gb.as_field(phi0), 5)
+    outb = to_np(outb)
+    for k, m in enumerate(members):
+        g = wd.Grid(m, prec, wd.UW)
+        out, _ = g.steps(gpu_params(wd, wd.UW, prm), g.as_field(phi0[k * N:(k + 1) * N]), 5)
+        np.testing.assert_array_equal(outb[k * N:(k + 1) * N], to_np(out))
+        og = oracle_grid(oracle, m, oracle.UW)
+        start = phi0[k * N:(k + 1) * N] if prec == 0 else to_np(g.as_field(phi0[k * N:(k + 1) * N]))
+        ref, _ = og.hj_steps(start, 5, **oracle_kw(oracle.UW, prm))
+        tol = 1e-10 if prec == 0 else 2e-5
+        np.testing.assert_allclose(outb[k * N:(k + 1) * N], ref, atol=tol * scale(ref), rtol=0)
+
+
+def test_levelset_stacked_grids(wd, oracle):
+    """The level-set march of a stack equals each member's march (bit for bit) and the
+    oracle's; the members' faces are independent (no bleeding across stacked grids)."""
+    members = _cyl_members([0.5, 0.45])
+    spec = W.stack(members)
+    N = members[0].N
+    fields = [np.hypot(*m.xyz) - 0.9 - 0.1 * k for k, m in enumerate(members)]
+    og = oracle_grid(oracle, members[0], oracle.E4)
+    dt = _ls_dt(og, 0.3)
+    gb = wd.Grid(spec, wd.FP64, wd.E4)
+    tb = gb.as_field(np.concatenate(fields))
+    gb.levelset(tb, 0.3, dt, 7)
+    outb = to_np(tb)
+    for k, m in enumerate(members):
+        g = wd.Grid(m, wd.FP64, wd.E4)
+        t = g.as_field(fields[k])
+        g.levelset(t, 0.3, dt, 7)
+        np.testing.assert_array_equal(outb[k * N:(k + 1) * N], to_np(t))
+        ref = oracle_grid(oracle, m, oracle.E4).levelset_steps(fields[k], 0.3, dt, 7)
+        np.testing.assert_allclose(outb[k * N:(k + 1) * N], ref, atol=1e-12 * scale(ref), rtol=0)
+
+
+def test_uw_duct_solve_properties(wd):
+    """UW Eikonal solve of a small duct in FP64: exact x-invariance (periodic direction,
+    x-independent data) and within the first-order error of min(y, 1-y, z, 1-z)."""
+    spec = W.duct(24, nx=8)
+    g = wd.Grid(spec, wd.FP64, wd.UW)
+    p = wd.default_params(wd.UW, equation=wd.EIKONAL, tol_l2=1e-11, max_iters=20000)
+    phi, st = g.solve(p)
+    assert st["converged"] == 1
+    P = to_np(phi).reshape(24, 24, 8)
+    assert np.abs(P - P[:, :, :1]).max() == 0.0
+    x, y, z = spec.xyz
+    ex = np.minimum.reduce([y, 1 - y, z, 1 - z])
+    assert np.abs(to_np(phi) - ex).max() < 0.75 / 23
