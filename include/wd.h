@@ -75,7 +75,9 @@ enum { WD_E2 = 0, WD_E4 = 1, WD_E6 = 2, WD_C4 = 3, WD_C6 = 4,
                                 of the HJ / Eikonal equations by first-order upwinding with the
                                 sign-selected slopes of Eqs. UW1-UW5; the metrics, the Laplacian
                                 and the Poisson guess by E2.  Runs on the generic per-operator
-                                path; wd_default_params turns the filter off for it. */
+                                path, so on single grids only (a stack of 2-D grids with WD_UW
+                                is WD_ERR_INVALID_ARG); wd_default_params turns the filter off
+                                for it. */
 
 /* initial guess */
 enum { WD_INIT_ZERO = 0,     /* phi = 0 (Sec. 3.5) */

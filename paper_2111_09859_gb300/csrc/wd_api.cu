@@ -228,6 +228,8 @@ static wd_status validate_desc(const wd_grid_desc* d)
     }
     if (d->precision < 0 || d->precision > 2) return set_error(WD_ERR_INVALID_ARG, "bad precision");
     if (d->scheme < WD_E2 || d->scheme > WD_UW) return set_error(WD_ERR_INVALID_ARG, "bad scheme");
+    if (d->scheme == WD_UW && d->ndim == 2 && d->n[2] > 1)
+        return set_error(WD_ERR_INVALID_ARG, "the upwind baseline runs on single grids (the generic path)");
     if (!(d->L_ref > 0.0)) return set_error(WD_ERR_INVALID_ARG, "L_ref must be positive");
     long long tot = (long long)((d->n[0] + 31) / 32 * 32) * d->n[1] * d->n[2];
     if (tot > (1LL << 31)) return set_error(WD_ERR_INVALID_ARG, "grid too large");
