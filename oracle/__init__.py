@@ -4,9 +4,10 @@ TEST INFRASTRUCTURE ONLY.  The oracle is imported by ``tests/``, by
 ``__graft_entry__.smoke()`` and by ``bench.py``'s CPU-baseline / reference leg, and by
 nothing else.  It shares no code with the CUDA path: the arithmetic lives in
 ``wd_oracle.c`` (plain C, one thread, double precision); this module compiles it with gcc
-and marshals numpy arrays through ctypes.  Two small pieces of the unsteady case are plain
-numpy here: the receding-surface update (Sec. 5.5) and the marching-squares length of a
-level set (the burning perimeter).
+and marshals numpy arrays through ctypes.  The baseline upwind scheme (Sec. 3.2.1) and the
+level-set march (Sec. 5.5) are in the C file too.  Two small pieces of the unsteady case are
+plain numpy here: the receding-surface update (Sec. 5.5) and the marching-squares length of
+a level set (the burning perimeter).
 
 Parity of every oracle function is pinned by ``tests/test_oracle_*.py`` against things
 other than the oracle itself: closed forms, polynomial exactness, Fourier symbols,

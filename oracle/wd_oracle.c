@@ -11,7 +11,9 @@
  * Parity pins (tests/test_oracle_*.py): polynomial exactness and modified wavenumbers of
  * the derivatives, the filter transfer function, dense solves of the tridiagonal systems,
  * analytic metrics of polar grids, the 1D Spalding identity, the exact linear fixed point,
- * closed-form distances and brute force.
+ * closed-form distances and brute force; for the baseline upwind scheme and the level-set
+ * march, Godunov's numerical Hamiltonian, linear fields on sheared grids, the exact channel
+ * distance, first-order convergence rates and the exact front speed.
  */
 #include <math.h>
 #include <stdlib.h>
