@@ -187,7 +187,7 @@ __device__ void f2_line_bc(const F2Args<T, M>& a, const LineMap& mp, const Slot 
 // its column directly (even reflection at non-periodic ends); a far-field / Neumann node
 // recomputes the stage values of its two inner neighbours (the same code, the same inputs
 // as their own threads, which write them too) to extrapolate, so no barrier is needed.
-template <typename T, typename M>
+template <typename T, typename M, bool POIS, bool LAD, bool CURV>
 __device__ __forceinline__ T f2_stage_value(const F2Args<T, M>& a, long long e, int j, bool own)
 {
     const Dims& D = a.D;
@@ -195,7 +195,7 @@ __device__ __forceinline__ T f2_stage_value(const F2Args<T, M>& a, long long e, 
     const long long st = D.stride(1);
     T Rv, dtv, gam = T(0), v = T(0), gm = T(0);
     const T lap = __ldg(a.LAP0 + e) + __ldg(a.LAP1 + e);
-    if (a.poisson) {
+    if (POIS) {
         Rv = T(1) + lap;                                                     // Eq. 19
     } else {
         M ux, uy;
@@ -205,8 +205,8 @@ __device__ __forceinline__ T f2_stage_value(const F2Args<T, M>& a, long long e, 
         gm = sqrt(g2);
         const T ph = __ldg(a.src + e);   // the stage input is never the stage output
         const T php = ph > T(0) ? ph : T(0);
-        if (a.equation == WD_HJ_STD) gam = T(a.eps) * php;                   // Eq. 6
-        else if (a.equation == WD_HJ_LAD) {                                  // Eq. 7
+        if (!LAD && a.equation == WD_HJ_STD) gam = T(a.eps) * php;           // Eq. 6
+        else if (LAD) {                                                      // Eq. 7
             // truncated Gaussian (Kawai & Lele) along direction 1 of C|LAD| smoothed along 0
             const T w[5] = {T(3565.0 / 10368.0), T(3091.0 / 12960.0), T(1997.0 / 25920.0),
                             T(149.0 / 12960.0), T(107.0 / 103680.0)};
@@ -227,7 +227,7 @@ __device__ __forceinline__ T f2_stage_value(const F2Args<T, M>& a, long long e, 
             const T g1 = T(a.eps) * php;
             gam = g1 < gl ? g1 : gl;
         }
-        if (a.curvature) {                                                   // Eq. 25
+        if (CURV) {                                                          // Eq. 25
             v = T(0.001) * (T(1) - gm) * (T(1) - gm);
             T corr = gm * (__ldg(a.KAP0 + e) + __ldg(a.KAP1 + e));
             corr = corr > T(0) ? corr : T(0);
@@ -237,7 +237,7 @@ __device__ __forceinline__ T f2_stage_value(const F2Args<T, M>& a, long long e, 
         }
     }
     if (a.stage == 0) {
-        if (a.poisson) dtv = T(a.cfl) / T(__ldg(a.sig2 + e));
+        if (POIS) dtv = T(a.cfl) / T(__ldg(a.sig2 + e));
         else {
             const T am = gm > T(1) ? gm : T(1);
             dtv = T(a.cfl) / (T(__ldg(a.sig1 + e)) * am + (gam + v) * T(__ldg(a.sig2 + e)));
@@ -263,7 +263,7 @@ __device__ __forceinline__ T f2_stage_value(const F2Args<T, M>& a, long long e, 
     return out;
 }
 
-template <typename T, typename M>
+template <typename T, typename M, bool POIS, bool LAD, bool CURV>
 __global__ void __launch_bounds__(512) k_f2_stage(F2Args<T, M> a)
 {
     // one thread per node: i from the x-blocks, j = blockIdx.y, the stacked grid = blockIdx.z
@@ -274,23 +274,23 @@ __global__ void __launch_bounds__(512) k_f2_stage(F2Args<T, M> a)
     const int j = blockIdx.y;
     const long long st = D.stride(1);
     const long long e = D.idx(i, j, blockIdx.z);
-    T out = f2_stage_value(a, e, j, true);
+    T out = f2_stage_value<T, M, POIS, LAD, CURV>(a, e, j, true);
     const int side = j == 0 ? 0 : (j == N1 - 1 ? 1 : -1);
     if (side >= 0) {
         int kind = side ? a.bchi1 : a.bclo1;
         if (kind == WD_BC_FARFIELD || kind == WD_BC_NEUMANN) {
-            if (a.poisson) kind = WD_BC_NEUMANN;
+            if (POIS) kind = WD_BC_NEUMANN;
             const long long s = side ? -st : st;
-            const T v1 = f2_stage_value(a, e + s, j + (side ? -1 : 1), false);
+            const T v1 = f2_stage_value<T, M, POIS, LAD, CURV>(a, e + s, j + (side ? -1 : 1), false);
             if (kind == WD_BC_NEUMANN) out = v1;
             else {
-                const T v2 = f2_stage_value(a, e + 2 * s, j + (side ? -2 : 2), false);
+                const T v2 = f2_stage_value<T, M, POIS, LAD, CURV>(a, e + 2 * s, j + (side ? -2 : 2), false);
                 const long long q = blockIdx.z;   // stacked grid
                 out = v1 + T((side ? a.ffr_hi : a.ffr_lo)[q + (long long)D.n[2] * i]) * (v1 - v2);
             }
         }
     }
-    if (a.mask[e]) out = a.poisson ? T(0) : a.dval[e];
+    if (a.mask[e]) out = POIS ? T(0) : a.dval[e];
     a.dst[e] = out;
 }
 
@@ -459,7 +459,14 @@ cudaError_t f2_launch(F2Args<T, M> a, int which, cudaStream_t st)
         const int row = (D.n[0] + 31) / 32 * 32;
         if (thr > row) thr = row;
         const dim3 grd((unsigned)((D.n[0] + thr - 1) / thr), (unsigned)D.n[1], (unsigned)D.n[2]);
-        k_f2_stage<T, M><<<grd, thr, 0, st>>>(a);
+        // the equation's branches as template flags, so that every load they guard can be
+        // issued ahead of the arithmetic
+        const bool lad = a.equation == WD_HJ_LAD, curv = a.curvature != 0;
+        if (a.poisson) k_f2_stage<T, M, true, false, false><<<grd, thr, 0, st>>>(a);
+        else if (lad && curv) k_f2_stage<T, M, false, true, true><<<grd, thr, 0, st>>>(a);
+        else if (lad) k_f2_stage<T, M, false, true, false><<<grd, thr, 0, st>>>(a);
+        else if (curv) k_f2_stage<T, M, false, false, true><<<grd, thr, 0, st>>>(a);
+        else k_f2_stage<T, M, false, false, false><<<grd, thr, 0, st>>>(a);
         return cudaGetLastError();
     }
     const size_t es = sizeof(T);
