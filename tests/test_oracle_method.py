@@ -38,6 +38,24 @@ def test_rhs_closed_form_quadratic(oracle, scheme, equation):
 
 
 @pytest.mark.parametrize("scheme", [1, 4])
+def test_rhs_linear_field_on_sheared_grid(oracle, scheme):
+    """On an affine, non-orthogonal grid the metrics are exact constants and a linear field
+    phi = a.x + c has U = a exactly at every node (Sec. 3.1 chain rule with all four metric
+    terms), lap = 0 and R = 1 - |a|^2."""
+    n = 12
+    i, j = np.meshgrid(np.arange(n), np.arange(n))
+    x = (i + 0.3 * j) / (n - 1)
+    y = (0.4 * i + j) / (n - 1)
+    g = oracle.Grid((n, n), np.stack([x.ravel(), y.ravel()]), (oracle.BC_FARFIELD,) * 2,
+                    (oracle.BC_FARFIELD,) * 2, scheme=scheme)
+    for a in ((0.7, 0.2), (-0.3, 0.9)):
+        phi = a[0] * x.ravel() + a[1] * y.ravel() + 0.1
+        for eq in (0, 2):
+            R, _ = g.rhs_hj(phi, equation=eq, scheme=scheme, eps=0.2)
+            np.testing.assert_allclose(R, 1 - a[0] ** 2 - a[1] ** 2, rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("scheme", [1, 4])
 def test_rhs_curvature_closed_form(oracle, scheme):
     """With the Nakanishi correction (Eq. 25) and phi = c0 + b x + c y (straight fronts),
     |U| = sqrt(b^2+c^2), n is constant so kappa = 0, lap = 0 and R = 1 - |U|^2."""
@@ -93,6 +111,28 @@ def test_lad_vanishes_on_linear_and_sees_a_kink(oracle):
     # far from the ridge (and walls) the field is linear: no diffusion
     assert np.abs(R_lad - R_eik)[far].max() < 1e-12
     assert (dt_lad[mid] < dt_eik[mid]).all()
+
+
+@pytest.mark.parametrize("lad_exp", [3.0, 4.0])
+def test_lad_closed_form_on_a_quartic(oracle, lad_exp):
+    """phi = a + b y + c y^4 on the channel (uniform h in y): the five-point fourth difference
+    of y^4 is 24 h^4 at every node, so the LAD term of Eq. 7 is C |(1/h)^4 h^exp 24 c h^4| =
+    24 C c h^exp at every node, and the Gaussian keeps a constant.  Below the cap eps phi,
+    R = 1 + Gamma lap - |U|^2 with lap = 12 c y^2 and U = b + 4 c y^3 (exact away from the
+    walls, where only centred rows are used)."""
+    sp = W.channel(16, 33)
+    g = grid_of(oracle, sp, 1)
+    y = sp.xyz[1]
+    h = 1.0 / 32
+    a, b, c, C = 0.3, 0.5, 0.2, 0.1
+    phi = a + b * y + c * y ** 4
+    R, _ = g.rhs_hj(phi, equation=1, scheme=1, eps=0.2, C_lad=C, lad_exp=lad_exp)
+    gam = 24 * C * c * h ** lad_exp
+    assert gam < (0.2 * phi).min()
+    ref = 1 + gam * 12 * c * y ** 2 - (b + 4 * c * y ** 3) ** 2
+    inner = (y > 4.5 * h) & (y < 1 - 4.5 * h)
+    np.testing.assert_allclose(R[inner], ref[inner], rtol=0, atol=1e-12)
+    assert np.abs(gam * 12 * c * y[inner] ** 2).max() > 1e3 * 1e-12   # the term is resolved
 
 
 def test_local_time_step_special_case(oracle):

@@ -1,0 +1,150 @@
+"""Planted mistakes in the oracle: each case copies the oracle's C source, plants one
+plausible mistake (a wrong coefficient, a flipped sign, a transposed index, a swapped
+operand, a dropped term), builds that copy apart from the real oracle, and runs the pins
+that guard the planted line against it: at least one must fail.  This shows that the pins
+constrain each part of the oracle they cover.  The oracle itself is never modified, and
+the copies live in pytest's temporary directory."""
+import importlib.util
+import os
+import shutil
+
+import pytest
+
+from tests import test_oracle_method as TM
+from tests import test_oracle_operators as TO
+from tests import test_oracle_rk4 as TR
+from tests import test_oracle_upwind as TU
+
+ORACLE_DIR = os.path.join(os.path.dirname(os.path.abspath(__file__)), os.pardir, "oracle")
+
+# (name, line as written in the oracle, the planted mistake, pins that must catch it)
+MUTANTS = [
+    ("E4 interior coefficient",
+     "(2.0 / 3.0) * (F(i + 1) - F(i - 1)) - (1.0 / 12.0) * (F(i + 2) - F(i - 2));",
+     "(2.0 / 3.0) * (F(i + 1) - F(i - 1)) - (1.0 / 6.0) * (F(i + 2) - F(i - 2));",
+     [(TO.test_deriv_interior_polynomial_order, dict(name="E4"))]),
+    ("C6 left coupling",
+     "            a[i] = 1.0 / 3.0;\n",
+     "            a[i] = 0.3;\n",
+     [(TO.test_deriv_periodic_symbol, dict(name="C6"))]),
+    ("one-sided boundary row",
+     "return (-25.0 * f0 + 48.0 * f1 - 36.0 * f2 + 16.0 * f3 - 3.0 * f4) / 12.0;",
+     "return (-25.0 * f0 + 48.0 * f1 - 36.0 * f2 + 16.0 * f3 - 4.0 * f4) / 12.0;",
+     [(TO.test_deriv_boundary_rows, {})]),
+    ("metric inverse transposed",
+     "C->xi[(l * 3 + m) * N + p] = (l < nd && m < nd) ? Mi[l][m] : 0.0;",
+     "C->xi[(l * 3 + m) * N + p] = (l < nd && m < nd) ? Mi[m][l] : 0.0;",
+     [(TO.test_metrics_uniform_and_affine, {})]),
+    ("filter coupling",
+     "        a[i] = al;\n        c[i] = al;\n",
+     "        a[i] = 0.5 * al;\n        c[i] = al;\n",
+     [(TO.test_filter_transfer_function_periodic, {})]),
+    ("fourth difference",
+     "out[i] = f[m2] - 4.0 * f[m1] + 6.0 * f[c] - 4.0 * f[p1] + f[p2];",
+     "out[i] = f[m2] - 4.0 * f[m1] + 5.0 * f[c] - 4.0 * f[p1] + f[p2];",
+     [(TM.test_lad_vanishes_on_linear_and_sees_a_kink, {}), (TM.test_lad_closed_form_on_a_quartic, dict(lad_exp=3.0))]),
+    ("LAD exponent",
+     "lad[p] += q * q * d4[p] * pow(C->dx[(size_t)l * N + p], P->lad_exp);",
+     "lad[p] += q * q * d4[p] * pow(C->dx[(size_t)l * N + p], P->lad_exp - 1.0);",
+     [(TM.test_lad_closed_form_on_a_quartic, dict(lad_exp=3.0))]),
+    ("LAD metric scale",
+     "lad[p] += q * q * d4[p] * pow(C->dx[(size_t)l * N + p], P->lad_exp);",
+     "lad[p] += q * d4[p] * pow(C->dx[(size_t)l * N + p], P->lad_exp);",
+     [(TM.test_lad_closed_form_on_a_quartic, dict(lad_exp=4.0))]),
+    ("Spalding root",
+     "phi[p] = -sqrt(g2) + sqrt(arg > 0.0 ? arg : 0.0);",
+     "phi[p] = sqrt(g2) + sqrt(arg > 0.0 ? arg : 0.0);",
+     [(TM.test_spalding_channel_exact, dict(scheme=1))]),
+    ("curvature correction sign",
+     "r = 1.0 + (gam + v) * (lap[p] - corr) - a2;",
+     "r = 1.0 + (gam + v) * (lap[p] + corr) - a2;",
+     [(TM.test_rhs_circle_curvature_sign, {})]),
+    ("standard diffusivity dropped",
+     "if (P->equation == OR_HJ_STD) gam = P->eps * phip;",
+     "if (P->equation == OR_HJ_STD) gam = 0.0;",
+     [(TM.test_rhs_closed_form_quadratic, dict(scheme=1, equation=0))]),
+    ("chain rule",
+     "for (int l = 0; l < nd; l++) s += C->xi[(l * 3 + m) * N + p] * D[(size_t)l * N + p];",
+     "for (int l = 0; l < nd; l++) s += C->xi[(l * 3 + m) * N + p] * D[(size_t)m * N + p];",
+     [(TM.test_rhs_closed_form_quadratic, dict(scheme=1, equation=2)),
+      (TM.test_rhs_linear_field_on_sheared_grid, dict(scheme=1))]),
+    ("Poisson source sign",
+     "R[p] = 1.0 + lap[p];",
+     "R[p] = 1.0 - lap[p];",
+     [(TM.test_poisson_fixed_point_and_convergence, {})]),
+    ("local step: diffusive term dropped",
+     "dt[p] = P->cfl / (metric_sum1(C, p) * a + (gam + v) * metric_sum2(C, p));",
+     "dt[p] = P->cfl / (metric_sum1(C, p) * a);",
+     [(TM.test_lad_vanishes_on_linear_and_sees_a_kink, {})]),
+    ("Dirichlet values",
+     "if (C->dmask[p]) phi[p] = poisson ? 0.0 : C->dval[p];",
+     "if (C->dmask[p]) phi[p] = 0.0;",
+     [(TM.test_bc_far_field_and_dirichlet, {})]),
+    ("far-field extrapolation sign",
+     "else phi[p] = phi[p + s] + rat[p] * (phi[p + s] - phi[p + 2 * s]);",
+     "else phi[p] = phi[p + s] - rat[p] * (phi[p + s] - phi[p + 2 * s]);",
+     [(TM.test_bc_far_field_and_dirichlet, {})]),
+    ("change norm over all nodes",
+     "*l2 = cnt ? sqrt(ss / cnt) : 0.0;",
+     "*l2 = cnt ? sqrt(ss / C->N) : 0.0;",
+     [(TM.test_step_norms_match_numpy, {})]),
+    ("pseudo-step RK4 weight",
+     "phi[p] = p0[p] + dt[p] / 6.0 * (K[0][p] + 2.0 * K[1][p] + 2.0 * K[2][p] + K[3][p]);",
+     "phi[p] = p0[p] + dt[p] / 6.0 * (K[0][p] + 2.0 * K[1][p] + K[2][p] + 2.0 * K[3][p]);",
+     [(TR.test_pseudo_step_is_classical_rk4, {})]),
+    ("upwind slope pairing as printed",
+     "return n_im1 * B + n_ip1 * F;",
+     "return n_im1 * F + n_ip1 * B;",
+     [(TU.test_upwind_slope_is_godunov, {})]),
+    ("upwind gradient with transposed metrics",
+     "for (int k = 0; k < nd; k++) Um[m] += C->xi[(k * 3 + m) * N + p] * sl[k];",
+     "for (int k = 0; k < nd; k++) Um[m] += C->xi[(m * 3 + k) * N + p] * sl[k];",
+     [(TU.test_advection_of_linear_field_on_sheared_grid, dict(a=(0.7, 0.2)))]),
+    ("upwind halves swapped",
+     "a += 0.5 * (uh + fabs(uh)) * B[(size_t)l * N + p] + 0.5 * (uh - fabs(uh)) * F[(size_t)l * N + p];",
+     "a += 0.5 * (uh + fabs(uh)) * F[(size_t)l * N + p] + 0.5 * (uh - fabs(uh)) * B[(size_t)l * N + p];",
+     [(TU.test_advection_of_monotone_field_is_first_order_upwind, {})]),
+    ("level-set speed sign",
+     "K[k][p] = -Fs * gm[p];",
+     "K[k][p] = Fs * gm[p];",
+     [(TU.test_levelset_planar_front_speed, {})]),
+    ("level-set RK4 stage from the wrong predecessor",
+     "for (int p = 0; p < N; p++) s[p] = p0[p] + cst[k] * dt * K[k - 1][p];",
+     "for (int p = 0; p < N; p++) s[p] = p0[p] + cst[k] * dt * K[0][p];",
+     [(TR.test_levelset_step_is_classical_rk4, {})]),
+    ("level-set faces not held",
+     "                if (on_face(g, p, d, side)) phi[p] = phi[p + s];",
+     "                if (on_face(g, p, d, side)) phi[p] = phi[p];",
+     [(TU.test_levelset_planar_front_speed, {})]),
+]
+
+
+def _mutant(tmp_path, line, planted):
+    src = open(os.path.join(ORACLE_DIR, "wd_oracle.c")).read()
+    assert src.count(line) == 1, f"the planting site must occur once: {line!r}"
+    (tmp_path / "wd_oracle.c").write_text(src.replace(line, planted))
+    shutil.copy(os.path.join(ORACLE_DIR, "wd_oracle.h"), tmp_path / "wd_oracle.h")
+    spec = importlib.util.spec_from_file_location("oracle_mutant", os.path.join(ORACLE_DIR, "__init__.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    mod._HERE = str(tmp_path)
+    mod._SRC = str(tmp_path / "wd_oracle.c")
+    mod._LIB = str(tmp_path / "libwd_oracle.so")
+    mod._lib = None
+    mod.build(force=True)
+    return mod
+
+
+@pytest.mark.parametrize("name,line,planted,pins", MUTANTS, ids=[m[0] for m in MUTANTS])
+def test_planted_mistake_is_caught(tmp_path, oracle, name, line, planted, pins):
+    # the pins pass on the real oracle
+    for fn, kw in pins:
+        fn(oracle, **kw)
+    mod = _mutant(tmp_path, line, planted)
+    caught = []
+    for fn, kw in pins:
+        try:
+            fn(mod, **kw)
+        except (AssertionError, ValueError, FloatingPointError):
+            caught.append(fn.__name__)
+    assert caught, f"no pin caught the planted mistake '{name}'"
