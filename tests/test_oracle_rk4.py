@@ -3,8 +3,8 @@ linear autonomous system y' = A y + b with step h:
 
     y_1 = y_0 + h T(hA) (A y_0 + b),   T(z) = 1 + z/2 + z^2/6 + z^3/24,
 
-the degree-4 Taylor polynomial of (exp(z) - 1) / z (the RK4 stability polynomial).  It is
-not the stage recursion: a wrong stage weight, a wrong stage abscissa or a stage built from
+the degree-3 Taylor polynomial of (exp(z) - 1) / z (1 + z T(z) is the RK4 stability
+polynomial).  It is not the stage recursion: a wrong stage weight, a wrong stage abscissa or a stage built from
 the wrong predecessor changes the polynomial.
 
 - Pseudo steps (Sec. 3.3): the Poisson pseudo-time equation (Eq. 19) on a doubly periodic
