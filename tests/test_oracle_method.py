@@ -135,6 +135,45 @@ def test_lad_closed_form_on_a_quartic(oracle, lad_exp):
     assert np.abs(gam * 12 * c * y[inner] ** 2).max() > 1e3 * 1e-12   # the term is resolved
 
 
+def test_lad_gaussian_removes_the_nyquist_mode(oracle):
+    """The quartic of the previous pin plus d (-1)^i along the periodic direction x: the
+    central derivatives of (-1)^i vanish, so U and lap keep their closed forms, while the
+    raw LAD field gains an alternating part C s_x 16 d (-1)^i (below the constant part, so
+    the absolute value does not fold it).  The Gaussian smoothing must remove it (its
+    transfer function is 1 at zero and 0 at the Nyquist wavenumber), leaving Gamma constant
+    and R as for the quartic alone."""
+    sp = W.channel(16, 33)
+    g = grid_of(oracle, sp, 1)
+    x, y = sp.xyz
+    i = np.rint(x * 16).astype(int)
+    h, hx = 1.0 / 32, 1.0 / 16
+    a, b, c, C, d = 0.3, 0.5, 0.2, 0.1, 2e-7
+    phi = a + b * y + c * y ** 4 + d * (-1.0) ** i
+    R, _ = g.rhs_hj(phi, equation=1, scheme=1, eps=0.2, C_lad=C, lad_exp=3.0)
+    gam = 24 * C * c * h ** 3
+    assert 16 * d * hx ** -1 < 24 * c * h ** 3       # the raw field keeps its sign
+    ref = 1 + gam * 12 * c * y ** 2 - (b + 4 * c * y ** 3) ** 2
+    inner = (y > 4.5 * h) & (y < 1 - 4.5 * h)
+    np.testing.assert_allclose(R[inner], ref[inner], rtol=0, atol=1e-13)
+
+
+def test_rhs_curvature_velocity_term(oracle):
+    """Eq. 25 with phi = c y^2 on the channel (y > 0): n = U / (|U| + eps0) is 1 up to
+    eps0, so kappa ~ eps0 / y^2 and the correction MAX(0, |U| kappa) ~ eps0 / y vanish, lap =
+    2c exactly, and R = 1 + (eps phi + 0.001 (1 - |U|)^2) 2c - |U|^2 with |U| = 2 c y."""
+    sp = W.channel(16, 33)
+    g = grid_of(oracle, sp, 1)
+    y = sp.xyz[1]
+    h, c = 1.0 / 32, 0.3
+    phi = c * y ** 2
+    R, _ = g.rhs_hj(phi, equation=0, scheme=1, eps=0.2, curvature=1, eps0=1e-8)
+    G = 2 * c * y
+    ref = 1 + (0.2 * phi + 0.001 * (1 - G) ** 2) * 2 * c - G ** 2
+    inner = (y > 0.25) & (y < 1 - 5.5 * h)
+    np.testing.assert_allclose(R[inner], ref[inner], rtol=0, atol=1e-7)
+    assert (0.001 * (1 - G[inner]) ** 2 * 2 * c).min() > 1e3 * 1e-7    # the term is resolved
+
+
 def test_local_time_step_special_case(oracle):
     """phi = 0 (zero gradient, zero diffusivity): dt = cfl / sum_l |grad xi_l|, i.e.
     cfl / (1/h0 + 1/h1) on a Cartesian grid."""

@@ -51,6 +51,14 @@ MUTANTS = [
      "lad[p] += q * q * d4[p] * pow(C->dx[(size_t)l * N + p], P->lad_exp);",
      "lad[p] += q * d4[p] * pow(C->dx[(size_t)l * N + p], P->lad_exp);",
      [(TM.test_lad_closed_form_on_a_quartic, dict(lad_exp=4.0))]),
+    ("LAD Gaussian weight",
+     "static const double gw[5] = {3565.0 / 10368.0, 3091.0 / 12960.0, 1997.0 / 25920.0,",
+     "static const double gw[5] = {3565.0 / 10368.0, 3091.0 / 12961.0, 1997.0 / 25920.0,",
+     [(TM.test_lad_gaussian_removes_the_nyquist_mode, {})]),
+    ("curvature velocity term",
+     "v = 0.001 * (1.0 - gm) * (1.0 - gm);",
+     "v = 0.002 * (1.0 - gm) * (1.0 - gm);",
+     [(TM.test_rhs_curvature_velocity_term, {})]),
     ("Spalding root",
      "phi[p] = -sqrt(g2) + sqrt(arg > 0.0 ? arg : 0.0);",
      "phi[p] = sqrt(g2) + sqrt(arg > 0.0 ? arg : 0.0);",
