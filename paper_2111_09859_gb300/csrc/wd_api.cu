@@ -191,7 +191,7 @@ static size_t footprint_bytes(const wd_grid_desc* d)
     if (!metric_double(d->precision)) b += (size_t)total * 4 * 9;
     b += (size_t)total * ms * (2 + 3);                  // sig1, sig2, lads
     b += (size_t)total * (2 + es);                      // wall, mask, dval
-    b += (size_t)total * es * W_NWORK;
+    b += (size_t)total * es * (W_NWORK - (d->scheme == WD_UW ? 0 : 1));   // W_ADV: baseline only
     long long fmax = 0;
     for (int k = 0; k < 3; k++) {
         long long f = (long long)d->n[(k + 1) % 3] * d->n[(k + 2) % 3];
@@ -1366,6 +1366,7 @@ static wd_status alloc_impl(wd_grid g)
     }
     ST(dmalloc(g, (void**)&g->dcount, sizeof(unsigned long long)));
     for (int k = 0; k < W_NWORK; k++) {
+        if (k == W_ADV && g->desc.scheme != WD_UW) continue;   // the upwind term: baseline only
         ST(dmalloc(g, &g->w[k], (size_t)tot * sizeof(T)));
         CK(cudaMemsetAsync(g->w[k], 0, (size_t)tot * sizeof(T), st));
     }

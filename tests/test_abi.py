@@ -52,6 +52,8 @@ def test_host_only_entry_points(libwd):
     b64 = libwd.footprint(W.cylinder(), libwd.FP64, libwd.C6)
     b32 = libwd.footprint(W.cylinder(), libwd.FP32, libwd.C6)
     assert b64 > b32 > 512 * 257 * 4 * 10
+    # the baseline upwind scheme holds one more state-size field (its advection term)
+    assert libwd.footprint(W.cylinder(), libwd.FP64, libwd.UW) - b64 == 512 * 257 * 8
     d = libwd.GridDesc()
     d.ndim = 2
     d.n[0], d.n[1], d.n[2] = 4, 16, 1      # too few nodes: rejected, footprint 0
