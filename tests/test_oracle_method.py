@@ -185,6 +185,29 @@ def test_local_time_step_special_case(oracle):
     np.testing.assert_allclose(dtp, 0.7 / (100.0 + 400.0), rtol=1e-12)
 
 
+def test_local_time_step_sheared_grid(oracle):
+    """On the affine grid x = (i + 0.3 j) h, y = (0.4 i + j) h the contravariant metrics are
+    the rows of the analytic inverse of [[1, 0.3], [0.4, 1]] / h, so the local step of
+    standard HJ on phi = a.x + c is cfl / (sigma_1 max(1, |a|) + eps phi sigma_2) with
+    sigma_1 = sum_l |grad xi_l| and sigma_2 = sum_l sum_k |grad xi_l . grad xi_k| (the
+    Gershgorin reading of the diffusive bound) from those exact metrics."""
+    n = 12
+    h = 1.0 / (n - 1)
+    i, j = np.meshgrid(np.arange(n), np.arange(n))
+    x = (i + 0.3 * j) * h
+    y = (0.4 * i + j) * h
+    g = oracle.Grid((n, n), np.stack([x.ravel(), y.ravel()]), (oracle.BC_FARFIELD,) * 2,
+                    (oracle.BC_FARFIELD,) * 2, scheme=1)
+    G = np.linalg.inv(np.array([[1.0, 0.3], [0.4, 1.0]]) * h)     # G[l] = grad xi_l
+    s1 = np.linalg.norm(G, axis=1).sum()
+    s2 = np.abs(G @ G.T).sum()
+    a = (0.7, 0.2)
+    phi = a[0] * x.ravel() + a[1] * y.ravel() + 0.4
+    _, dt = g.rhs_hj(phi, equation=0, scheme=1, eps=0.2, cfl=0.8)
+    ref = 0.8 / (s1 * max(1.0, np.hypot(*a)) + 0.2 * phi * s2)
+    np.testing.assert_allclose(dt, ref, rtol=1e-12)
+
+
 @pytest.mark.parametrize("scheme", [1, 4])
 def test_spalding_channel_exact(oracle, scheme):
     """Channel of unit height: phi' = y (1 - y) / 2 solves lap = -1 with phi' = 0 at both

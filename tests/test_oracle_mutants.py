@@ -100,6 +100,42 @@ MUTANTS = [
      "phi[p] = p0[p] + dt[p] / 6.0 * (K[0][p] + 2.0 * K[1][p] + 2.0 * K[2][p] + K[3][p]);",
      "phi[p] = p0[p] + dt[p] / 6.0 * (K[0][p] + 2.0 * K[1][p] + K[2][p] + 2.0 * K[3][p]);",
      [(TR.test_pseudo_step_is_classical_rk4, {})]),
+    ("cyclic correction sign",
+     "for (int i = 0; i < n; i++) x[i] -= f * z[i];",
+     "for (int i = 0; i < n; i++) x[i] += f * z[i];",
+     [(TO.test_tridiag_matches_dense_solve, dict(cyclic=True))]),
+    ("filter coefficient of the 8th-order member",
+     "a[2] = (-7.0 + 14.0 * al) / 32.0;",
+     "a[2] = (-7.0 + 14.0 * al) / 31.0;",
+     [(TO.test_filter_coefficients_solve_their_defining_conditions, dict(hw=4, al=0.49))]),
+    ("filter order near an end",
+     "            if (e < hw) hw = e;",
+     "            if (e < hw) hw = e + 1 < 5 ? e + 1 : 5;",
+     [(TO.test_filter_nonperiodic_ends, {})]),
+    ("periodic metric shift dropped",
+     "for (int p = 0; p < N; p++) A[(m * 3 + l) * N + p] = dtmp[p] + shift / (double)n;",
+     "for (int p = 0; p < N; p++) A[(m * 3 + l) * N + p] = dtmp[p];",
+     [(TO.test_metrics_periodic_shift, {})]),
+    ("spacing with a transposed Jacobian",
+     "for (int m = 0; m < nd; m++) s += M[m][l] * M[m][l];",
+     "for (int m = 0; m < nd; m++) s += M[l][m] * M[l][m];",
+     [(TO.test_metrics_uniform_and_affine, {})]),
+    ("far-field spacing ratio inverted",
+     "r[p] = dist_nodes(C, p, p1) / dist_nodes(C, p1, p2);",
+     "r[p] = dist_nodes(C, p1, p2) / dist_nodes(C, p, p1);",
+     [(TM.test_bc_far_field_and_dirichlet, {})]),
+    ("time-step metric sum without the square root",
+     "        s += sqrt(q);\n    }\n    return s;\n}\n\n/* sum_l sum_k",
+     "        s += q;\n    }\n    return s;\n}\n\n/* sum_l sum_k",
+     [(TM.test_local_time_step_special_case, {})]),
+    ("Gershgorin cross terms dropped",
+     "                q += C->xi[(l * 3 + m) * C->N + p] * C->xi[(k * 3 + m) * C->N + p];\n            s += fabs(q);",
+     "                q += C->xi[(l * 3 + m) * C->N + p] * C->xi[(k * 3 + m) * C->N + p];\n            s += l == k ? fabs(q) : 0.0;",
+     [(TM.test_local_time_step_special_case, {}), (TM.test_local_time_step_sheared_grid, {})]),
+    ("level-set selection not mirrored for F < 0",
+     "double sg = Fs < 0.0 ? -1.0 : 1.0;",
+     "double sg = 1.0;",
+     [(TU.test_levelset_negative_speed_shrinks, {})]),
     ("upwind slope pairing as printed",
      "return n_im1 * B + n_ip1 * F;",
      "return n_im1 * F + n_ip1 * B;",
