@@ -114,20 +114,21 @@ def test_lad_vanishes_on_linear_and_sees_a_kink(oracle):
 
 
 @pytest.mark.parametrize("lad_exp", [3.0, 4.0])
-def test_lad_closed_form_on_a_quartic(oracle, lad_exp):
+@pytest.mark.parametrize("c", [0.2, -0.2])
+def test_lad_closed_form_on_a_quartic(oracle, lad_exp, c):
     """phi = a + b y + c y^4 on the channel (uniform h in y): the five-point fourth difference
     of y^4 is 24 h^4 at every node, so the LAD term of Eq. 7 is C |(1/h)^4 h^exp 24 c h^4| =
-    24 C c h^exp at every node, and the Gaussian keeps a constant.  Below the cap eps phi,
-    R = 1 + Gamma lap - |U|^2 with lap = 12 c y^2 and U = b + 4 c y^3 (exact away from the
+    24 C |c| h^exp at every node (either sign of c), and the Gaussian keeps a constant.  Below
+    the cap eps phi, R = 1 + Gamma lap - |U|^2 with lap = 12 c y^2 and U = b + 4 c y^3 (exact away from the
     walls, where only centred rows are used)."""
     sp = W.channel(16, 33)
     g = grid_of(oracle, sp, 1)
     y = sp.xyz[1]
     h = 1.0 / 32
-    a, b, c, C = 0.3, 0.5, 0.2, 0.1
+    a, b, C = 0.3, 0.5, 0.1
     phi = a + b * y + c * y ** 4
     R, _ = g.rhs_hj(phi, equation=1, scheme=1, eps=0.2, C_lad=C, lad_exp=lad_exp)
-    gam = 24 * C * c * h ** lad_exp
+    gam = 24 * C * abs(c) * h ** lad_exp
     assert gam < (0.2 * phi).min()
     ref = 1 + gam * 12 * c * y ** 2 - (b + 4 * c * y ** 3) ** 2
     inner = (y > 4.5 * h) & (y < 1 - 4.5 * h)
@@ -241,6 +242,19 @@ def test_poisson_fixed_point_and_convergence(oracle):
     # the filtered fixed point sits close to the quadratic (the order-2 filter rows next
     # to the walls do not preserve quadratics, so it is not exactly on it)
     assert np.abs(p - ex).max() < 1e-4
+
+
+def test_poisson_far_field_is_neumann(oracle):
+    """The auxiliary Poisson problem takes d(phi')/dn = 0 on far-field faces (Sec. 3.5):
+    after Poisson steps on the plate (wall y = 0, far field y = 1, stretched so that the
+    HJ extrapolation would give another value) every far-field node holds its inner
+    neighbour's value."""
+    sp = W.plate(8, 33, 1.0, stretch=1.05)
+    g = grid_of(oracle, sp, 1)
+    p, st = g.poisson_steps(np.zeros(sp.N), 50, filter=0, cfl=0.8)
+    P = p.reshape(33, 8)
+    assert np.abs(P[-2] - P[-3]).min() > 1e-6        # an extrapolation would differ
+    np.testing.assert_array_equal(P[-1], P[-2])
 
 
 @pytest.mark.parametrize("scheme", [1, 2, 4])

@@ -13,6 +13,7 @@ import pytest
 from tests import test_oracle_method as TM
 from tests import test_oracle_operators as TO
 from tests import test_oracle_rk4 as TR
+from tests import test_oracle_star as TS
 from tests import test_oracle_upwind as TU
 
 ORACLE_DIR = os.path.join(os.path.dirname(os.path.abspath(__file__)), os.pardir, "oracle")
@@ -42,15 +43,15 @@ MUTANTS = [
     ("fourth difference",
      "out[i] = f[m2] - 4.0 * f[m1] + 6.0 * f[c] - 4.0 * f[p1] + f[p2];",
      "out[i] = f[m2] - 4.0 * f[m1] + 5.0 * f[c] - 4.0 * f[p1] + f[p2];",
-     [(TM.test_lad_vanishes_on_linear_and_sees_a_kink, {}), (TM.test_lad_closed_form_on_a_quartic, dict(lad_exp=3.0))]),
+     [(TM.test_lad_vanishes_on_linear_and_sees_a_kink, {}), (TM.test_lad_closed_form_on_a_quartic, dict(lad_exp=3.0, c=0.2))]),
     ("LAD exponent",
      "lad[p] += q * q * d4[p] * pow(C->dx[(size_t)l * N + p], P->lad_exp);",
      "lad[p] += q * q * d4[p] * pow(C->dx[(size_t)l * N + p], P->lad_exp - 1.0);",
-     [(TM.test_lad_closed_form_on_a_quartic, dict(lad_exp=3.0))]),
+     [(TM.test_lad_closed_form_on_a_quartic, dict(lad_exp=3.0, c=0.2))]),
     ("LAD metric scale",
      "lad[p] += q * q * d4[p] * pow(C->dx[(size_t)l * N + p], P->lad_exp);",
      "lad[p] += q * d4[p] * pow(C->dx[(size_t)l * N + p], P->lad_exp);",
-     [(TM.test_lad_closed_form_on_a_quartic, dict(lad_exp=4.0))]),
+     [(TM.test_lad_closed_form_on_a_quartic, dict(lad_exp=4.0, c=0.2))]),
     ("LAD Gaussian weight",
      "static const double gw[5] = {3565.0 / 10368.0, 3091.0 / 12960.0, 1997.0 / 25920.0,",
      "static const double gw[5] = {3565.0 / 10368.0, 3091.0 / 12961.0, 1997.0 / 25920.0,",
@@ -136,6 +137,30 @@ MUTANTS = [
      "double sg = Fs < 0.0 ? -1.0 : 1.0;",
      "double sg = 1.0;",
      [(TU.test_levelset_negative_speed_shrinks, {})]),
+    ("C4 coefficient",
+     "d[i] = 1.5 * (f[ip] - f[im]) / 2.0;",
+     "d[i] = 1.4 * (f[ip] - f[im]) / 2.0;",
+     [(TO.test_deriv_periodic_symbol, dict(name="C4"))]),
+    ("LAD cap as a maximum",
+     "gam = a < b ? a : b;\n        } else gam = 0.0;",
+     "gam = a > b ? a : b;\n        } else gam = 0.0;",
+     [(TM.test_lad_closed_form_on_a_quartic, dict(lad_exp=3.0, c=0.2))]),
+    ("LAD magnitude without the absolute value",
+     "for (int p = 0; p < N; p++) lad[p] = P->C_lad * fabs(lad[p]);",
+     "for (int p = 0; p < N; p++) lad[p] = P->C_lad * lad[p];",
+     [(TM.test_lad_closed_form_on_a_quartic, dict(lad_exp=3.0, c=-0.2))]),
+    ("Poisson far field kept as extrapolation",
+     "            if (poisson) bc = OR_BC_NEUMANN;\n",
+     "",
+     [(TM.test_poisson_fixed_point_and_convergence, {}), (TM.test_poisson_far_field_is_neumann, {})]),
+    ("level length: crossing interpolated from the wrong end",
+     "t = np.where(h, V[a] / (V[a] - V[b]), 0.0)",
+     "t = np.where(h, V[b] / (V[a] - V[b]), 0.0)",
+     [(TS.test_level_length_straight_lines_exact, dict(a=1.0, b=-2.0, c=0.25, length=None))]),
+    ("recede: floor as a ceiling",
+     "dval = np.where(mask == 1, np.maximum(new, floor), 0.0)",
+     "dval = np.where(mask == 1, np.minimum(new, floor), 0.0)",
+     [(TS.test_recede_definition, {})]),
     ("upwind slope pairing as printed",
      "return n_im1 * B + n_ip1 * F;",
      "return n_im1 * F + n_ip1 * B;",
@@ -164,16 +189,21 @@ MUTANTS = [
 
 
 def _mutant(tmp_path, line, planted):
-    src = open(os.path.join(ORACLE_DIR, "wd_oracle.c")).read()
-    assert src.count(line) == 1, f"the planting site must occur once: {line!r}"
-    (tmp_path / "wd_oracle.c").write_text(src.replace(line, planted))
+    """A copy of the oracle (C source, header and the Python wrapper) in tmp_path with the
+    mistake planted in whichever file holds the line, loaded as a separate module."""
+    target = None
+    for f in ("wd_oracle.c", "__init__.py"):
+        src = open(os.path.join(ORACLE_DIR, f)).read()
+        if line in src:
+            assert src.count(line) == 1 and target is None, f"the planting site must occur once: {line!r}"
+            target = f
+            src = src.replace(line, planted)
+        (tmp_path / f).write_text(src)
+    assert target, f"planting site not found: {line!r}"
     shutil.copy(os.path.join(ORACLE_DIR, "wd_oracle.h"), tmp_path / "wd_oracle.h")
-    spec = importlib.util.spec_from_file_location("oracle_mutant", os.path.join(ORACLE_DIR, "__init__.py"))
+    spec = importlib.util.spec_from_file_location("oracle_mutant", str(tmp_path / "__init__.py"))
     mod = importlib.util.module_from_spec(spec)
     spec.loader.exec_module(mod)
-    mod._HERE = str(tmp_path)
-    mod._SRC = str(tmp_path / "wd_oracle.c")
-    mod._LIB = str(tmp_path / "libwd_oracle.so")
     mod._lib = None
     mod.build(force=True)
     return mod
