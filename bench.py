@@ -340,6 +340,10 @@ def run_native(args, rank, world):
             out["square65"] = square_report(wd)
             out["upwind_vs_central"] = upwind_report(wd)
             out["levelset_regression"] = levelset_report(wd)
+        fp64, _ = wd.fma_probe(wd.FP64, 4096)
+        fp32, _ = wd.fma_probe(wd.FP32, 65536)
+        out["fma_probe_tflops"] = {"fp64": round(fp64, 2), "fp32": round(fp32, 2),
+                                   "what": "wd_fma_probe: 8 independent FMA chains per thread"}
         out["cpu_baseline"] = cpu_baseline()
         print(json.dumps(out), flush=True)
     if world > 1:

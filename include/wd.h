@@ -232,6 +232,15 @@ wd_status wd_profile(wd_grid g, int enable);
  * profiling was enabled; synchronises the stream. */
 wd_status wd_profile_read(wd_grid g, int cls, double* ms_total, long long* launches);
 
+/* Arithmetic-rate probe: the fused multiply-add throughput of the current device in TFLOP/s
+ * (2 flops per FMA) for precision WD_FP64 or WD_FP32, from one timed launch (after one
+ * warm-up) of 8 independent FMA chains per thread, 8 blocks of 256 threads per SM, iters
+ * steps per chain; *ms gets the launch's device time.  Synchronous, on the legacy default
+ * stream; allocates and frees its own small output buffer.  It measures the ALU ceiling that
+ * the FP64 form of the solver is compared with.
+ * Errors: WD_ERR_INVALID_ARG for another precision or iters outside [1, 2^24]. */
+wd_status wd_fma_probe(int precision, int iters, double* tflops, double* ms);
+
 /* ---- allocation-free variant (no counterpart in the paper) ---------------------------- */
 
 /* Change norms of two state arrays with no device allocation at all, for callers that must

@@ -94,6 +94,7 @@ SIGNATURES = {
     "wd_recede": (_i, [_vp, _vp, _d, _d, _vp, _vp]),
     "wd_level_length": (_i, [_vp, _vp, _d, C.POINTER(C.c_double)]),
     "wd_levelset": (_i, [_vp, _vp, _d, _d, _i]),
+    "wd_fma_probe": (_i, [_i, _i, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "wd_server_create": (_i, [C.POINTER(ServerConfig), C.POINTER(_vp)]),
     "wd_server_submit": (_i, [_vp, C.POINTER(GridDesc), _vp, _vp, _vp, C.POINTER(SolveParams), _vp,
                               C.POINTER(C.c_longlong)]),
@@ -355,6 +356,13 @@ class Grid:
         self._sync_stream()
         _check(lib().wd_get_metrics(self._h, _ptr(xi), _ptr(J), _ptr(dx)))
         return xi.view(3, 3, self.N), J, dx.view(3, self.N)
+
+
+def fma_probe(precision=FP64, iters=4096):
+    """(TFLOP/s, ms) of the device's FMA rate in the given precision (wd_fma_probe)."""
+    tf, ms = C.c_double(), C.c_double()
+    _check(lib().wd_fma_probe(precision, int(iters), C.byref(tf), C.byref(ms)))
+    return tf.value, ms.value
 
 
 def solve_batch(grids, params, phis):
