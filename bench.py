@@ -302,6 +302,7 @@ def run_native(args, rank, world):
                 "peak_source": src + " (of " + src + ")", "unit": "GB/s", "frac": round(ach / peak, 4),
                 "traffic": PROFILED_TRAFFIC.get(best), "algorithmic_bytes_per_launch": ab,
                 "avg_launch_us": round(kms / kn * 1e3, 3),
+                "frac_of_nominal_7900": round(ach / 7900.0, 4),
                 "share_of_timed": round(kms / max(1e-9, sum(v[0] for v in prof.values())), 3)}
     launches = sum(v[1] for v in prof.values())
 
