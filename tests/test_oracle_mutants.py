@@ -161,6 +161,26 @@ MUTANTS = [
      "dval = np.where(mask == 1, np.maximum(new, floor), 0.0)",
      "dval = np.where(mask == 1, np.minimum(new, floor), 0.0)",
      [(TS.test_recede_definition, {})]),
+    ("Thomas forward elimination",
+     "double m = b[i] - a[i] * cp[i - 1];",
+     "double m = b[i] - c[i] * cp[i - 1];",
+     [(TO.test_tridiag_matches_dense_solve, dict(cyclic=False))]),
+    ("E6 third-neighbour coefficient",
+     "+ (1.0 / 60.0) * (F(i + 3) - F(i - 3));",
+     "+ (1.0 / 50.0) * (F(i + 3) - F(i - 3));",
+     [(TO.test_deriv_interior_polynomial_order, dict(name="E6"))]),
+    ("C6 right-hand side",
+     "d[i] = (14.0 / 9.0) * (f[ip] - f[im]) / 2.0 + (1.0 / 9.0) * (f[ip2] - f[im2]) / 4.0;",
+     "d[i] = (14.0 / 9.0) * (f[ip] - f[im]) / 2.0 + (1.0 / 9.0) * (f[ip2] - f[im2]) / 2.0;",
+     [(TO.test_deriv_periodic_symbol, dict(name="C6"))]),
+    ("Jacobian determinant term",
+     "- A[0][1] * (A[1][0] * A[2][2] - A[1][2] * A[2][0])",
+     "+ A[0][1] * (A[1][0] * A[2][2] - A[1][2] * A[2][0])",
+     [(TO.test_metrics_uniform_and_affine, {})]),
+    ("wall faces not Dirichlet",
+     "                    C->dmask[p] = 1;\n                    C->dval[p] = 0.0;",
+     "                    C->dval[p] = 0.0;",
+     [(TM.test_flat_wall_linear_fixed_point, dict(scheme=1, equation=0, curv=0))]),
     ("upwind slope pairing as printed",
      "return n_im1 * B + n_ip1 * F;",
      "return n_im1 * F + n_ip1 * B;",
