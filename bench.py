@@ -114,7 +114,8 @@ def peak_hbm():
 
 # DRAM bytes (read + write) per launch of the kernel classes of this workload, from one ncu
 # capture of the current kernels (k_p2_div2, both directions in one launch: 54.8 MB read +
-# 14.2 MB written, against 67.4 MB of algorithmic bytes).
+# 14.2 MB written, against 84.2 MB of algorithmic bytes; the other divergence parts are
+# still in L2 when the launch ends).
 PROFILED_TRAFFIC = {"div": 68.97e6}
 
 
@@ -125,7 +126,8 @@ def algorithmic_bytes(cls, nodes, nd, es, ms, curv, lad=True):
       deriv  phi in, d(phi)/dxi_l out; LAD: s_l in and, for direction 1, s_1 d4_1(phi)
              out; direction 0 (half of the launches) reads it back and writes the smoothed
              C|LAD| instead
-      div    D_0, D_1 and the 4 metrics of U in, the divergence part(s) out
+      div    one launch does both directions (k_p2_div2): D_0, D_1 and the 4 metric arrays
+             of U in, once; each direction's divergence part(s) out
       point  stage kernel: 13 state-size arrays in, the stage value and the RK4
              accumulator out, plus the Dirichlet flags
       filter / norm: the field in and out (norm: plus the old state and the flags)"""
@@ -133,7 +135,7 @@ def algorithmic_bytes(cls, nodes, nd, es, ms, curv, lad=True):
         return int(nodes * (2 * es + ((1.5 * es + ms) if lad else 0)))
     if cls == "div":
         nout = 2 if curv else 1
-        return int(nodes * (2 * es + 4 * ms + nout * es))
+        return int(nodes * (2 * es + 4 * ms + 2 * nout * es))
     if cls == "point":
         return nodes * (15 * es + 1)
     if cls == "filter":
