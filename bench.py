@@ -128,8 +128,9 @@ def algorithmic_bytes(cls, nodes, nd, es, ms, curv, lad=True):
              C|LAD| instead
       div    one launch does both directions (k_p2_div2): D_0, D_1 and the 4 metric arrays
              of U in, once; each direction's divergence part(s) out
-      point  stage kernel: 13 state-size arrays in, the stage value and the RK4
-             accumulator out, plus the Dirichlet flags
+      point  stage kernel (LAD + curvature): 11 state-size arrays in (Lap_0, Lap_1,
+             kappa_0, kappa_1, D_0, D_1, phi_s, G_0, phi^n, acc, dt) and the 4 metric arrays
+             of U, the stage value and the RK4 accumulator out, plus the Dirichlet flags
       filter / norm: the field in and out (norm: plus the old state and the flags)"""
     if cls == "deriv":
         return int(nodes * (2 * es + ((1.5 * es + ms) if lad else 0)))
@@ -137,7 +138,7 @@ def algorithmic_bytes(cls, nodes, nd, es, ms, curv, lad=True):
         nout = 2 if curv else 1
         return int(nodes * (2 * es + 4 * ms + 2 * nout * es))
     if cls == "point":
-        return nodes * (15 * es + 1)
+        return nodes * (13 * es + 4 * ms + 1)
     if cls == "filter":
         return nodes * 2 * es
     if cls == "norm":

@@ -13,4 +13,6 @@ def test_algorithmic_bytes_of_the_cylinder_batch():
     assert bench.algorithmic_bytes("div", n, 2, es, ms, True) == n * (2 * es + 4 * ms + 4 * es)
     assert bench.algorithmic_bytes("div", n, 2, es, ms, False) == n * (2 * es + 4 * ms + 2 * es)
     assert bench.algorithmic_bytes("div", n, 2, es, ms, True) == 84213760
+    # the stage: 11 state-size fields and 4 metric arrays in, the stage value and acc out, flags
+    assert bench.algorithmic_bytes("point", n, 2, es, ms, True) == n * (13 * es + 4 * ms + 1)
     assert bench.algorithmic_bytes("gauss", n, 2, es, ms, True) is None
