@@ -1,5 +1,6 @@
-"""Host logic of the ctypes binding (no GPU): the grid descriptor and arrays built from a
-GridSpec, and the library's footprint query for the descriptors the workloads produce."""
+"""Host logic (no GPU): the grid descriptor and arrays the ctypes binding builds from a
+GridSpec, the library's footprint query for the workloads' descriptors, and the index
+argument behind the level-set stage kernel's folded face conditions."""
 import ctypes as C
 
 import numpy as np
@@ -46,3 +47,49 @@ def test_footprint_of_the_workloads():
     three = fp(W.stack([one, one, one]), wd.FP32_METRIC64, wd.C6)
     assert 2.5 * a32 < three < 3.0 * a32 + (1 << 20)
     assert fp(W.duct(16, nx=8), wd.FP32_METRIC64, wd.E6) > 0
+
+
+def _faces_by_copies(V, periodic):
+    """Zero-gradient faces as the oracle applies them: direction by direction (0, 1, 2 =
+    the last, middle and first numpy axes), each non-periodic face node takes its inner
+    neighbour's current value."""
+    A = V.copy()
+    nd = A.ndim
+    for d in range(nd):
+        if periodic[d]:
+            continue
+        ax = nd - 1 - d
+        lo = [slice(None)] * nd
+        lo1 = [slice(None)] * nd
+        lo[ax], lo1[ax] = 0, 1
+        A[tuple(lo)] = A[tuple(lo1)]
+        hi = [slice(None)] * nd
+        hi1 = [slice(None)] * nd
+        hi[ax], hi1[ax] = -1, -2
+        A[tuple(hi)] = A[tuple(hi1)]
+    return A
+
+
+def _faces_by_clamping(V, periodic):
+    """The level-set stage kernel's form: every node takes the value of the node whose
+    non-periodic coordinates are clamped to [1, n - 2]."""
+    nd = V.ndim
+    idx = []
+    for ax in range(nd):
+        d = nd - 1 - ax
+        n = V.shape[ax]
+        i = np.arange(n)
+        idx.append(i if periodic[d] else np.clip(i, 1, n - 2))
+    return V[np.ix_(*idx)]
+
+
+def test_level_set_faces_fold_into_the_stage():
+    """The level-set stage kernel stores at each face node the stage value of its clamped
+    interior node instead of running face-copy launches; the two agree for every grid shape,
+    corners and edges included."""
+    rng = np.random.default_rng(9)
+    for shape, periodic in (((9, 8), (False, False)), ((9, 8), (True, False)),
+                            ((6, 7, 8), (False, False, False)), ((6, 7, 8), (True, False, False)),
+                            ((6, 7, 8), (False, True, False))):
+        V = rng.standard_normal(shape)
+        np.testing.assert_array_equal(_faces_by_clamping(V, periodic), _faces_by_copies(V, periodic))
