@@ -50,6 +50,25 @@ def test_advection_of_linear_field_on_sheared_grid(oracle, a):
         np.testing.assert_allclose(gm[inner.ravel()], np.hypot(*a), rtol=1e-12)
 
 
+def test_upwind_terms_of_a_linear_field_on_an_affine_3d_grid(oracle):
+    """3-D affine map x = M (i, j, k) + c: every one-sided difference of a linear field is
+    exact, so the advection term is |a|^2 and the level-set |grad phi| is |a| at the interior
+    nodes, for fronts along any direction (all nine metric terms enter)."""
+    M = np.array([[0.9, 0.2, -0.1], [0.05, 1.1, 0.3], [0.15, -0.2, 0.8]]) * 0.1
+    n = (9, 10, 11)
+    K, J, I = np.meshgrid(np.arange(n[2]), np.arange(n[1]), np.arange(n[0]), indexing="ij")
+    idx = np.stack([I.reshape(-1), J.reshape(-1), K.reshape(-1)]).astype(float)
+    xyz = M @ idx + np.array([[0.3], [-0.2], [1.0]])
+    g = oracle.Grid(n, xyz, (oracle.BC_FARFIELD,) * 3, (oracle.BC_FARFIELD,) * 3, scheme=oracle.UW)
+    inner = ((I > 0) & (I < n[0] - 1) & (J > 0) & (J < n[1] - 1) & (K > 0) & (K < n[2] - 1)).reshape(-1)
+    for a in ((0.6, 0.3, -0.5), (-0.2, -0.7, 0.4)):
+        phi = np.asarray(a) @ xyz + 0.2
+        adv = g.upwind_advection(phi)
+        np.testing.assert_allclose(adv[inner], np.dot(a, a), rtol=1e-11)
+        for F in (0.3, -0.3):
+            np.testing.assert_allclose(g.levelset_gradmag(phi, F)[inner], np.linalg.norm(a), rtol=1e-11)
+
+
 def test_advection_of_monotone_field_is_first_order_upwind(oracle):
     """Uniform Cartesian grid, phi increasing along both directions: the term is
     sum_l (B_l / h_l)^2 with the backward differences; decreasing: the forward ones."""
