@@ -13,6 +13,7 @@ device time.  Ranks solve their own batches (weak scaling, no collective on the 
 rank 0 prints one JSON line.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
+    python bench.py --case NAME [--steps K] [--warmup W] [--timer]   (profiling cases)
 """
 from __future__ import annotations
 
@@ -344,10 +345,6 @@ def run_native(args, rank, world):
             out["square65"] = square_report(wd)
             out["upwind_vs_central"] = upwind_report(wd)
             out["levelset_regression"] = levelset_report(wd)
-        fp64, _ = wd.fma_probe(wd.FP64, 4096)
-        fp32, _ = wd.fma_probe(wd.FP32, 65536)
-        out["fma_probe_tflops"] = {"fp64": round(fp64, 2), "fp32": round(fp32, 2),
-                                   "what": "wd_fma_probe: 8 independent FMA chains per thread"}
         out["cpu_baseline"] = cpu_baseline()
         print(json.dumps(out), flush=True)
     if world > 1:
@@ -652,6 +649,100 @@ def run_reference(args, rank, world):
     }), flush=True)
 
 
+CASES = """
+  cyl16     16 stacked cylinder O-grids 257 x 512, C6 + LAD + curvature, alpha_f 0.495,
+            FP32 state (metrics computed in FP64)
+  cyl16-64  the same 16 cylinders in FP64
+  duct256   square duct 256^3, E6 + LAD, FP32
+  duct128   square duct 128^3 (a small case of the same kernels)
+  star1025  star port 1025^2, E4 + LAD, FP32
+  star1025-ls  the same star, level-set steps (F = 0.3, dt = 0.5 h / F) instead of pseudo
+            steps, from the exact signed distance
+  chan-uw   channel 1024 x 513, baseline upwind scheme, standard HJ, FP64 (generic path)
+  ell2048   one ellipse O-grid 1025 x 2048, C6 + LAD, FP32"""
+
+
+def build_case(name):
+    """(spec, precision, scheme, params, initial field) of a --case workload: the exact
+    distance where one exists, a smooth random field otherwise, so that the steps run in the
+    converged regime."""
+    import numpy as np
+
+    from paper_2111_09859_gb300 import workloads as W, wd
+
+    if name.startswith("cyl16"):
+        spec = W.stack([W.cylinder(257, 512, 1.03, r_wall=0.5 * (1 + 0.01 * k)) for k in range(16)])
+        prec = wd.FP64 if name == "cyl16-64" else wd.FP32_METRIC64
+        p = wd.default_params(wd.C6, equation=wd.HJ_LAD, curvature=1, alpha_f=0.495)
+        x, y = spec.xyz
+        r0 = np.repeat([0.5 * (1 + 0.01 * k) for k in range(16)], 257 * 512)
+        return spec, prec, wd.C6, p, np.hypot(x, y) - r0
+    if name.startswith("duct"):
+        n = int(name[4:])
+        spec = W.duct(n)
+        p = wd.default_params(wd.E6, equation=wd.HJ_LAD)
+        x, y, z = spec.xyz
+        return spec, wd.FP32_METRIC64, wd.E6, p, np.minimum.reduce([y, 1 - y, z, 1 - z])
+    if name == "chan-uw":
+        spec = W.channel(1024, 513)
+        p = wd.default_params(wd.UW, equation=wd.HJ_STD)
+        y = spec.xyz[1]
+        return spec, wd.FP64, wd.UW, p, np.minimum(y, 1.0 - y)
+    if name.startswith("star1025"):
+        spec = W.star(1025)
+        p = wd.default_params(wd.E4, equation=wd.HJ_LAD, eps=0.15, alpha_f=0.45, lad_exp=4.0)
+        sd = spec.meta["signed_distance"]
+        return spec, wd.FP32_METRIC64, wd.E4, p, np.where(spec.mask == 1, spec.dval, sd)
+    if name == "ell2048":
+        spec = W.ellipse(1025, 2048, 2.0)
+        p = wd.default_params(wd.C6, equation=wd.HJ_LAD)
+        return spec, wd.FP32_METRIC64, wd.C6, p, 0.3 * W.random_field(spec, 1) + np.hypot(*spec.xyz)
+    raise SystemExit(f"unknown case {name}")
+
+
+
+def run_case(args):
+    """--case NAME: W pseudo steps (or level-set steps), then K timed ones, of a named
+    workload; one line per run.  For profilers (ncu) and quick per-class kernel timings
+    (--timer: the library's CUDA-event timer around every launch).  Not a bench line."""
+    import torch
+
+    from paper_2111_09859_gb300 import build as B
+
+    B.build()
+    from paper_2111_09859_gb300 import wd
+
+    spec, prec, scheme, p, phi0 = build_case(args.case)
+    g = wd.Grid(spec, prec, scheme)
+    if args.case.endswith("-ls"):
+        phi = g.as_field(spec.meta["signed_distance"])
+        F = 0.3
+        ls_dt = 0.5 * spec.meta["h"] / F
+
+        def run(n):
+            g.levelset(phi, F, ls_dt, n)
+    else:
+        phi = g.as_field(phi0)
+
+        def run(n):
+            g.steps(p, phi, n)
+    run(args.warmup)
+    torch.cuda.synchronize()
+    if args.timer:
+        g.profile(True)
+    t = time.time()
+    run(args.steps)
+    torch.cuda.synchronize()
+    dt = time.time() - t
+    line = f"{args.case}: {spec.N} nodes, {args.steps} steps, {dt / max(args.steps, 1) * 1e3:.3f} ms/step"
+    if args.timer:
+        prof = g.profile_read()
+        g.profile(False)
+        line += " | " + ", ".join(f"{k} {v[0] / max(v[1], 1) * 1e3:.1f} us x{v[1]}" for k, v in prof.items() if v[1])
+    print(line, flush=True)
+    g.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -660,7 +751,12 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--full", action="store_true", help="serving: 1000 requests; star: 200 steps")
     ap.add_argument("--no-extras", action="store_true", help="only the headline cylinder workload")
+    ap.add_argument("--case", default=None, help="run pseudo steps of a named workload (profiling):" + CASES)
+    ap.add_argument("--timer", action="store_true", help="--case: per-class kernel timer")
     args = ap.parse_args()
+    if args.case:
+        run_case(args)
+        return
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
     if args.impl == "reference":

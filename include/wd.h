@@ -232,32 +232,27 @@ wd_status wd_profile(wd_grid g, int enable);
  * profiling was enabled; synchronises the stream. */
 wd_status wd_profile_read(wd_grid g, int cls, double* ms_total, long long* launches);
 
-/* Arithmetic-rate probe: the fused multiply-add throughput of the current device in TFLOP/s
- * (2 flops per FMA) for precision WD_FP64 or WD_FP32, from one timed launch (after one
- * warm-up) of 8 independent FMA chains per thread, 8 blocks of 256 threads per SM, iters
- * steps per chain; *ms gets the launch's device time.  Synchronous, on the legacy default
- * stream; allocates and frees its own small output buffer.  It measures the ALU ceiling that
- * the FP64 form of the solver is compared with.
- * Errors: WD_ERR_INVALID_ARG for another precision or iters outside [1, 2^24]. */
-wd_status wd_fma_probe(int precision, int iters, double* tflops, double* ms);
-
 /* ---- allocation-free variant (no counterpart in the paper) ---------------------------- */
 
-/* Change norms of two state arrays with no device allocation at all, for callers that must
- * not allocate: code running while a CUDA stream capture is open, applications whose own
- * pool already owns the device memory, latency-critical loops that forbid allocator calls.
- * Computes what the solver's change-norm step computes (Eq. 20): over the n entries whose
- * mask_dev byte is 0 (mask_dev NULL: all entries), norms_dev[0] = RMS(new - old) / scale and
- * norms_dev[1] = max|new - old| / scale, accumulated in double in a fixed order.
+/* Change norms of two state arrays with no device allocation at all.  The paper has no
+ * counterpart: this entry point exists for callers that cannot allocate device memory,
+ * e.g. an application whose own memory pool has already taken the device memory (a
+ * cudaMalloc would fail or evict its pool), or a real-time loop that must not call the
+ * allocator (cudaMalloc / cudaFree can synchronise the device and stall every stream).
+ * It computes what the solver's convergence check computes: over the n entries whose
+ * mask_dev byte is 0 (mask_dev NULL: all entries), norms_dev[0] = RMS(new - old) / scale
+ * and norms_dev[1] = max|new - old| / scale, accumulated in double in a fixed order.
  *   new_dev, old_dev  device arrays of n values: double for WD_FP64, float otherwise
  *   mask_dev          device array of n bytes, or NULL
  *   norms_dev         caller-owned device array of 2 doubles (written)
  *   cuda_stream       cudaStream_t the work is enqueued on (the call does not wait)
- * Scratch: one library-owned file-scope device array of about 25 KB per GPU that loads the
- * library, held until the process exits; no cudaMalloc / cudaFree ever runs.  The first
- * call on a device looks up that array's device address, so make that first call before
- * any stream capture begins.  Every call shares the array: calls whose kernels overlap on
- * the GPU (different streams without ordering) race and give wrong norms.
+ * All arrays must be on the current device.  Scratch: one library-owned file-scope device
+ * array of about 25 KB per GPU that loads the library, held until the process exits; no
+ * cudaMalloc / cudaFree ever runs.  The first call on a device looks up that array's
+ * device address and keeps it for the process, so do not call this entry point on a device
+ * after cudaDeviceReset.  Every call shares the array and clears its arrival counter
+ * first: calls whose kernels overlap on the GPU (different streams without ordering) race
+ * and give wrong norms.
  * Errors: WD_ERR_INVALID_ARG for NULL arrays, n outside [1, 2^30] (the maximum size),
  * a bad precision or scale <= 0; WD_ERR_CUDA if the launch fails. */
 wd_status wd_change_norms_noalloc(const void* new_dev, const void* old_dev,

@@ -4,9 +4,13 @@
 // nodes whose mask byte is 0, accumulated in double with a fixed block partition and a
 // fixed final order), but its scratch (the per-block partial sums and the arrival
 // counter) lives in the file-scope array below, so a call allocates nothing.  It serves
-// callers that must not allocate device memory: code running while a CUDA stream capture
-// is open (allocation calls break the capture), applications whose own memory pool already
-// owns the device memory, and latency-critical loops that forbid allocator calls.
+// callers that cannot allocate device memory: an application whose own memory pool has
+// already taken the device memory, or a real-time loop that must not call the allocator
+// (cudaMalloc / cudaFree can synchronise the device).  The paper has no counterpart.
+//
+// The array's device address is looked up once per device, on the first call with that
+// device current, and kept for the process; a cudaDeviceReset invalidates it, so the entry
+// point is not for use on a device after a reset.
 #include <mutex>
 
 #include "wd_api_internal.h"

@@ -94,7 +94,6 @@ SIGNATURES = {
     "wd_recede": (_i, [_vp, _vp, _d, _d, _vp, _vp]),
     "wd_level_length": (_i, [_vp, _vp, _d, C.POINTER(C.c_double)]),
     "wd_levelset": (_i, [_vp, _vp, _d, _d, _i]),
-    "wd_fma_probe": (_i, [_i, _i, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "wd_server_create": (_i, [C.POINTER(ServerConfig), C.POINTER(_vp)]),
     "wd_server_submit": (_i, [_vp, C.POINTER(GridDesc), _vp, _vp, _vp, C.POINTER(SolveParams), _vp,
                               C.POINTER(C.c_longlong)]),
@@ -358,13 +357,6 @@ class Grid:
         return xi.view(3, 3, self.N), J, dx.view(3, self.N)
 
 
-def fma_probe(precision=FP64, iters=4096):
-    """(TFLOP/s, ms) of the device's FMA rate in the given precision (wd_fma_probe)."""
-    tf, ms = C.c_double(), C.c_double()
-    _check(lib().wd_fma_probe(precision, int(iters), C.byref(tf), C.byref(ms)))
-    return tf.value, ms.value
-
-
 def solve_batch(grids, params, phis):
     n = len(grids)
     hs = (C.c_void_p * n)(*[g._h for g in grids])
@@ -390,15 +382,48 @@ def footprint(spec, precision=FP64, scheme=E4):
     return lib().wd_query_footprint(C.byref(d), None)
 
 
-def change_norms_noalloc(new, old, mask=None, scale=1.0, stream=None):
-    """RMS and max of new - old over entries with mask == 0, through the allocation-free
-    entry point; returns a device tensor of 2 doubles (enqueued on the stream)."""
+def _noalloc_inputs(new, old, mask, out):
+    """Checks the arrays of change_norms_noalloc before anything reaches the library, so
+    that a wrong dtype, length or layout can never make the kernel read past an array:
+    new and old of float32 or float64 with the same dtype and length, contiguous; mask
+    None or a contiguous uint8 / bool tensor of the same length; out None or a contiguous
+    float64 tensor of 2 entries; every tensor on one CUDA device (checked last).  Returns
+    the precision code of the state."""
     import torch
 
-    prec = FP64 if new.dtype == torch.float64 else FP32
-    out = torch.empty(2, dtype=torch.float64, device=new.device)
-    _check(lib().wd_change_norms_noalloc(_ptr(new), _ptr(old), _ptr(mask), new.numel(), prec,
-                                         float(scale), _ptr(out), _stream_handle(stream)))
+    if new.dtype not in (torch.float32, torch.float64):
+        raise ValueError(f"change_norms_noalloc: new must be float32 or float64, not {new.dtype}")
+    if old.dtype != new.dtype:
+        raise ValueError(f"change_norms_noalloc: old is {old.dtype}, new is {new.dtype}")
+    if old.numel() != new.numel() or new.numel() == 0:
+        raise ValueError(f"change_norms_noalloc: lengths differ or are zero ({new.numel()}, {old.numel()})")
+    if mask is not None and (mask.dtype not in (torch.uint8, torch.bool) or mask.numel() != new.numel()):
+        raise ValueError("change_norms_noalloc: mask must be uint8 / bool with one entry per node")
+    if out is not None and (out.dtype != torch.float64 or out.numel() != 2):
+        raise ValueError("change_norms_noalloc: out must be a float64 tensor of 2 entries")
+    ts = [t for t in (new, old, mask, out) if t is not None]
+    if not all(t.is_contiguous() for t in ts):
+        raise ValueError("change_norms_noalloc: every tensor must be contiguous")
+    if not all(t.is_cuda and t.device == new.device for t in ts):
+        raise ValueError("change_norms_noalloc: every tensor must be on the same CUDA device")
+    return FP64 if new.dtype == torch.float64 else FP32
+
+
+def change_norms_noalloc(new, old, mask=None, scale=1.0, stream=None, out=None):
+    """RMS and max of new - old over entries with mask == 0, through the allocation-free
+    entry point (wd_change_norms_noalloc); returns ``out`` (a device tensor of 2 doubles,
+    created here when None), enqueued on ``stream`` (default: the current stream of the
+    tensors' device).  The call runs with the tensors' device current, because the library
+    finds its scratch array on the current device."""
+    import torch
+
+    prec = _noalloc_inputs(new, old, mask, out)
+    with torch.cuda.device(new.device):
+        if out is None:
+            out = torch.empty(2, dtype=torch.float64, device=new.device)
+        s = stream if stream is not None else torch.cuda.current_stream(new.device)
+        _check(lib().wd_change_norms_noalloc(_ptr(new), _ptr(old), _ptr(mask), new.numel(), prec,
+                                             float(scale), _ptr(out), C.c_void_p(s.cuda_stream)))
     return out
 
 

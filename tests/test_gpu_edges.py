@@ -151,15 +151,3 @@ def test_duct_full_size_properties(wd):
     assert err.max() <= 1.5 * h and np.sqrt((err ** 2).mean()) <= 0.1 * h
     g.close()
 
-
-def test_fma_probe(wd):
-    """The arithmetic-rate probe returns finite positive rates, FP32 above FP64, and rejects
-    bad arguments."""
-    import ctypes as C
-
-    f64, ms64 = wd.fma_probe(wd.FP64, 2048)
-    f32, ms32 = wd.fma_probe(wd.FP32, 32768)
-    assert 0.0 < f64 < f32 < 1000.0 and ms64 > 0.0 and ms32 > 0.0
-    t, m = C.c_double(), C.c_double()
-    assert wd.lib().wd_fma_probe(wd.FP32_METRIC64, 10, C.byref(t), C.byref(m)) == wd.ERR_INVALID_ARG
-    assert wd.lib().wd_fma_probe(wd.FP64, 0, C.byref(t), C.byref(m)) == wd.ERR_INVALID_ARG

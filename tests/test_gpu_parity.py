@@ -2,9 +2,10 @@
 oracle on identical seeded inputs, at sizes the oracle finishes in seconds that still
 span several line chunks, shared-memory tiles and ragged tails.
 
-Tolerances (written here, derived in the design doc): FP64 operators agree to 1e-11 of the
-field scale (only summation order and FMA contraction differ); FP32 operators to 2e-6 of
-the scale; FP64 full solves to 1e-6 L and FP32 full solves to 2e-4 L."""
+Tolerances: FP64 operators agree to 1e-11 of the field scale (only summation order and FMA
+contraction differ); FP32 operators to 2e-6 of the scale (float rounding of a few dozen
+operations, amplified by the filter and derivative weights where noted); FP64 full solves
+to 1e-6 L and FP32 full solves to 2e-4 L."""
 import numpy as np
 import pytest
 
