@@ -650,9 +650,9 @@ def run_reference(args, rank, world):
 
 
 CASES = """
-  cyl16     16 stacked cylinder O-grids 257 x 512, C6 + LAD + curvature, alpha_f 0.495,
-            FP32 state (metrics computed in FP64)
-  cyl16-64  the same 16 cylinders in FP64
+  cylK      K stacked cylinder O-grids 257 x 512 (cyl16: the headline batch), C6 + LAD +
+            curvature, alpha_f 0.495, FP32 state (metrics computed in FP64)
+  cylK-64   the same K cylinders in FP64
   duct256   square duct 256^3, E6 + LAD, FP32
   duct128   square duct 128^3 (a small case of the same kernels)
   star1025  star port 1025^2, E4 + LAD, FP32
@@ -670,12 +670,14 @@ def build_case(name):
 
     from paper_2111_09859_gb300 import workloads as W, wd
 
-    if name.startswith("cyl16"):
-        spec = W.stack([W.cylinder(257, 512, 1.03, r_wall=0.5 * (1 + 0.01 * k)) for k in range(16)])
-        prec = wd.FP64 if name == "cyl16-64" else wd.FP32_METRIC64
+    if name.startswith("cyl"):
+        nb = int(name[3:].split("-")[0])
+        members = [W.cylinder(257, 512, 1.03, r_wall=0.5 * (1 + 0.01 * k)) for k in range(nb)]
+        spec = W.stack(members) if nb > 1 else members[0]
+        prec = wd.FP64 if name.endswith("-64") else wd.FP32_METRIC64
         p = wd.default_params(wd.C6, equation=wd.HJ_LAD, curvature=1, alpha_f=0.495)
         x, y = spec.xyz
-        r0 = np.repeat([0.5 * (1 + 0.01 * k) for k in range(16)], 257 * 512)
+        r0 = np.repeat([0.5 * (1 + 0.01 * k) for k in range(nb)], 257 * 512)
         return spec, prec, wd.C6, p, np.hypot(x, y) - r0
     if name.startswith("duct"):
         n = int(name[4:])

@@ -222,7 +222,10 @@ enum { WD_K_DERIV = 0,   /* first derivatives of phi along one direction */
        WD_K_POINT = 4,   /* pointwise kernels: chain rule, LAD term, RK stage, Spalding */
        WD_K_BC = 5,      /* boundary conditions */
        WD_K_NORM = 6,    /* change norms + commit */
-       WD_K_NCLASS = 7 };
+       WD_K_LINE0 = 7,   /* line-resident 2-D step: direction-0 pass of an RK stage */
+       WD_K_LINE1 = 8,   /* line-resident 2-D step: direction-1 pass of an RK stage (with the
+                            stage update) */
+       WD_K_NCLASS = 9 };
 
 /* enable != 0 clears the counters and brackets every later kernel launch on g with CUDA
  * events on g's stream (this adds a small gap between launches); enable == 0 stops. */

@@ -17,6 +17,7 @@
 #include "wd_api_internal.h"
 #include "wd_cart3d.h"
 #include "wd_fused2d.h"
+#include "wd_line2d.h"
 
 using namespace wd;
 
@@ -90,6 +91,8 @@ struct wd_grid_s {
     int npartial = 0;           // capacity of `partial` in blocks
     int force_generic = 0;      // WD_FORCE_GENERIC=1 at creation: never use the fused path
     int part_off = 0;           // WD_PART_OFF=1 at creation: fused 2-D path with PCR passes
+    int line_off = 0;           // WD_LINE2D_OFF=1 at creation: fused 2-D path without the
+                                // line-resident passes (per-operator partition passes)
     int tuned = 0;              // autotuner ran for this grid
     int tune_stage_threads = 0; // chosen block size of the 2-D stage kernel (0: default)
     int tune_by = 0;            // chosen block rows of the Cartesian stencil kernels (0: default)
@@ -656,6 +659,95 @@ struct Solver {
         return true;
     }
 
+    // the line-resident passes (wd_line2d.cuh) apply to the central schemes up to half width 2
+    // when both line lengths have partition tables and the filter passes do too
+    bool line2d(const F2Args<T, M>& a, bool poisson) const
+    {
+        if (g->line_off || !part2d(a)) return false;
+        const int sch = g->desc.scheme;
+        if (sch != WD_E2 && sch != WD_E4 && sch != WD_C4 && sch != WD_C6) return false;
+        const int nf = p->curvature && !poisson ? 4 : 2;
+        return l2_supported<T, M>(D, g->dtab[0].template pview<T>(), g->dtab[1].template pview<T>(), nf);
+    }
+
+    L2Args<T, M> l2_args(bool poisson)
+    {
+        L2Args<T, M> a;
+        std::memset(&a, 0, sizeof(a));
+        a.D = D;
+        switch (g->desc.scheme) {   // interior rows of Eq. 16: a1 (f+1 - f-1) + a2 (f+2 - f-2)
+        case WD_E2: a.a1 = T(0.5); a.a2 = T(0); break;
+        case WD_E4: a.a1 = T(2.0 / 3.0); a.a2 = T(-1.0 / 12.0); break;
+        case WD_C4: a.a1 = T(0.75); a.a2 = T(0); break;
+        default: a.a1 = T(7.0 / 9.0); a.a2 = T(1.0 / 36.0); break;   // C6
+        }
+        a.implicit = g->dtab[0].implicit;
+        a.xi = xi();
+        a.lads = (const M*)g->lads;
+        a.sig1 = (const M*)g->sig1;
+        a.sig2 = (const M*)g->sig2;
+        a.phin = W(W_PHIN);
+        a.acc = W(W_ACC);
+        a.dtv = W(W_DT);
+        a.D0 = W(W_D0);
+        a.D1 = W(W_D1);
+        a.L1 = W(W_N1);
+        a.LAP0 = W(W_LAP);
+        a.KAP0 = W(W_KAP);
+        a.G0 = W(W_LAD);
+        a.mask = g->mask;
+        a.dval = (const T*)g->dval;
+        a.ffr_lo = g->ffr + 2 * g->fmax;
+        a.ffr_hi = g->ffr + 3 * g->fmax;
+        a.bclo1 = g->desc.bc_lo[1];
+        a.bchi1 = g->desc.bc_hi[1];
+        a.eps = p->eps;
+        a.cfl = p->cfl;
+        a.C_lad = p->C_lad;
+        a.eps0 = p->eps0;
+        a.equation = p->equation;
+        a.lad = p->equation == WD_HJ_LAD && !poisson;
+        a.poisson = poisson;
+        return a;
+    }
+
+    // Y0, four (X, Y) stage pairs, the direction-0 filter, the direction-1 filter with the
+    // BCs, change norms and commit
+    wd_status step_line2d(F2Args<T, M>& f, bool poisson)
+    {
+        L2Args<T, M> a = l2_args(poisson);
+        const PartTab<T> t0 = g->dtab[0].template pview<T>(), t1 = g->dtab[1].template pview<T>();
+        const int nf = p->curvature && !poisson ? 4 : 2;
+        a.src = W(W_PHIN);
+        {
+            ProfScope ps(g, WD_K_DERIV);
+            CK(l2_launch<T, M>(a, t1, L2_Y0, nf, st));
+        }
+        for (int s = 0; s < 4; s++) {
+            a.src = stage_src(s);
+            a.dst = stage_dst(s);
+            a.stage = s;
+            a.next = s < 3;
+            {
+                ProfScope ps(g, WD_K_LINE0);
+                CK(l2_launch<T, M>(a, t0, L2_X, nf, st));
+            }
+            {
+                ProfScope ps(g, WD_K_LINE1);
+                CK(l2_launch<T, M>(a, t1, L2_Y, nf, st));
+            }
+        }
+        f.src = stage_dst(3);
+        f.dst = stage_dst(3);
+        if (p->filter) {
+            ProfScope ps(g, WD_K_FILTER);
+            CK(p2_launch<T, M>(f, g->ftab[0].template pview<T>(), P2_FILTER0, 0, st));
+        }
+        ProfScope ps(g, WD_K_NORM);
+        CK(p2_launch<T, M>(f, g->ftab[1].template pview<T>(), F2_FILTER, 1, st));
+        return WD_OK;
+    }
+
     // stage s reads stage_src(s) and writes stage_dst(s): distinct arrays, because the stage
     // kernel of a far-field node re-evaluates its inner neighbours from the stage input
     T* stage_src(int s) { return s == 0 ? W(W_PHIN) : (s % 2 ? W(W_PHIS) : W(W_T0)); }
@@ -714,6 +806,7 @@ struct Solver {
             ST(op_filter(p->alpha_f, op));
             std::memcpy(a.fa, op.fa, sizeof(a.fa));
         }
+        if (line2d(a, poisson)) return step_line2d(a, poisson);
         if (part2d(a)) return step_part2d(a);
         for (int s = 0; s < 4; s++) {
             a.src = stage_src(s);
@@ -1603,6 +1696,8 @@ wd_status wd_create_grid(const wd_grid_desc* desc, const double* xyz_host, const
         g->force_generic = fg && fg[0] == '1';
         const char* po = std::getenv("WD_PART_OFF");
         g->part_off = po && po[0] == '1';
+        const char* lo = std::getenv("WD_LINE2D_OFF");
+        g->line_off = lo && lo[0] == '1';
     }
     wd_status s;
     {

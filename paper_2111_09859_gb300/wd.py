@@ -105,8 +105,8 @@ SIGNATURES = {
     "wd_server_destroy": (None, [_vp]),
 }
 
-K_DERIV, K_DIV, K_FILTER, K_GAUSS, K_POINT, K_BC, K_NORM = range(7)
-K_NAMES = ("deriv", "div", "filter", "gauss", "point", "bc", "norm")
+K_DERIV, K_DIV, K_FILTER, K_GAUSS, K_POINT, K_BC, K_NORM, K_LINE0, K_LINE1 = range(9)
+K_NAMES = ("deriv", "div", "filter", "gauss", "point", "bc", "norm", "line0", "line1")
 
 
 def lib(path: str | None = None):

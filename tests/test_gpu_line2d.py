@@ -1,0 +1,147 @@
+"""The line-resident 2-D pseudo step (wd_line2d.cuh: two line passes per RK stage) against the
+FP64 oracle, and against the per-operator partition passes it replaces (WD_LINE2D_OFF=1), on
+grids whose line lengths have partition tables (128 / 256 / 512 ... periodic, 65 / 129 / 257
+... non-periodic), so that the new passes actually run.
+
+Tolerances as in test_gpu_parity: pseudo steps 1e-10 (FP64) / 1e-5 (FP32) of the field
+scale after 4 steps; full solves 1e-6 L (FP64) / 2e-4 L (FP32); the two GPU paths, which
+solve the same systems in a different order, 1e-11 (FP64) / 2e-5 (FP32) of the scale."""
+import numpy as np
+import pytest
+
+from paper_2111_09859_gb300 import workloads as W
+from tests.helpers import base_params, gpu_params, oracle_grid, oracle_kw, to_np
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def wd():
+    import torch
+
+    assert torch.cuda.is_available()
+    from paper_2111_09859_gb300 import build, wd as _wd
+
+    build.build()
+    return _wd
+
+
+def scale(a):
+    return max(1.0, float(np.abs(a).max()))
+
+
+def _cyl(nr, nt, r_wall=0.5):
+    return W.cylinder(nr, nt, 1.03 ** (256 / (nr - 1)), r_wall=r_wall)
+
+
+def _radial_start(spec):
+    """distance-like start: radial distance from the wall node of each ray (0 on the wall)"""
+    r = np.hypot(*spec.xyz[:2])
+    rr = r.reshape(-1, spec.shape[1], spec.shape[0])
+    return (rr - rr[:, :1, :]).reshape(-1)
+
+
+CASES = {
+    # name: (spec maker, scheme, params)
+    "cyl65x128-C6-lad-curv": (lambda: _cyl(65, 128), 4, dict(equation=1, curvature=1, alpha_f=0.495)),
+    "cyl129x256-C4-std": (lambda: _cyl(129, 256), 3, dict(equation=0)),
+    "ellipse65x128-C6-lad": (lambda: W.ellipse(65, 128, 2.5), 4, dict(equation=1)),
+    "channel256x129-E4-lad": (lambda: W.channel(256, 129), 1, dict(equation=1)),
+    "channel128x65-E2-eik": (lambda: W.channel(128, 65), 0, dict(equation=2)),
+    "plate128x97-C6-lad": (lambda: W.plate(128, 97, height=2.0, stretch=1.03), 4, dict(equation=1)),   # FP32: see below
+    "stack3-cyl65x128-C6-lad-curv": (lambda: W.stack([_cyl(65, 128, r) for r in (0.5, 0.45, 0.55)]), 4,
+                                     dict(equation=1, curvature=1, alpha_f=0.495)),
+}
+
+
+def _start(spec):
+    if spec.name == "channel":
+        y = spec.xyz[1]
+        return np.minimum(y, 1 - y)
+    if spec.name == "plate":
+        return spec.xyz[1].copy()
+    return _radial_start(spec)
+
+
+def _members(spec):
+    if spec.batch == 1:
+        return [spec]
+    n1 = spec.N // spec.batch
+    return [W.GridSpec(spec.name, spec.shape, spec.xyz[:, k * n1:(k + 1) * n1], spec.bc_lo, spec.bc_hi,
+                       period=spec.period, L_ref=spec.L_ref, meta=spec.meta["members"][k])
+            for k in range(spec.batch)]
+
+
+@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("prec", [0, 1])
+def test_line2d_steps_match_oracle(wd, oracle, name, prec):
+    mk, scheme, kw = CASES[name]
+    spec = mk()
+    prm = base_params(scheme, **kw)
+    members = _members(spec)
+    n1 = spec.N // spec.batch
+    raw = _start(spec) + 0.02 * W.random_field(spec, 11)
+    ogs = [oracle_grid(oracle, m, scheme) for m in members]
+    phi0 = np.concatenate([og.apply_bc(raw[k * n1:(k + 1) * n1]) for k, og in enumerate(ogs)])
+    g = wd.Grid(spec, prec, scheme)
+    out, st = g.steps(gpu_params(wd, scheme, prm), g.as_field(phi0), 4, kind=0)
+    outp, _ = g.steps(gpu_params(wd, scheme, prm), g.as_field(np.zeros(spec.N)), 20, kind=1)
+    out, outp = to_np(out), to_np(outp)
+    tol = 1e-10 if prec == 0 else 1e-5
+    if prec == 1 and name.startswith("plate"):
+        # FP32 on this stretched plate: the per-operator passes (WD_LINE2D_OFF=1) differ from
+        # the oracle by the same 9.1e-5 after 4 steps as the line-resident passes (FP64 agrees
+        # to 4e-12): float rounding of the LAD fourth differences (s_0 = 128) amplified by the
+        # alpha_f = 0.49 filter, not a difference between the GPU paths; bound at the FP32
+        # solve bar
+        tol = 1e-4
+    worst = 0.0
+    for k, og in enumerate(ogs):
+        sl = slice(k * n1, (k + 1) * n1)
+        ref, ost = og.hj_steps(phi0[sl], 4, **oracle_kw(scheme, prm))
+        np.testing.assert_allclose(out[sl], ref, atol=tol * scale(ref), rtol=0)
+        worst = max(worst, ost["res_l2"])
+        refp, _ = og.poisson_steps(np.zeros(n1), 20, **oracle_kw(scheme, prm))
+        np.testing.assert_allclose(outp[sl], refp, atol=tol * scale(refp), rtol=0)
+    assert st["res_l2"] == pytest.approx(worst, rel=1e-8 if prec == 0 else 1e-2)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_line2d_full_solve_matches_oracle(wd, oracle, prec):
+    spec = _cyl(65, 128)
+    prm = base_params(4, equation=1, curvature=1, alpha_f=0.495, tol_l2=1e-10 if prec == 0 else 1e-7)
+    ref, ost = oracle_grid(oracle, spec, 4).solve(**oracle_kw(4, dict(prm, tol_l2=1e-12)))
+    assert ost["converged"]
+    g = wd.Grid(spec, prec, 4)
+    out, st = g.solve(gpu_params(wd, 4, prm))
+    assert st["converged"], st
+    err = float(np.abs(to_np(out) - ref).max())
+    assert err <= (1e-6 if prec == 0 else 2e-4) * spec.L_ref, err
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("gname", ["cyl16x257x512", "ellipse513x1024", "ellipse1025x2048", "channel512x257"])
+def test_line2d_matches_partition_passes(wd, monkeypatch, prec, gname):
+    """The same pseudo steps (HJ and Poisson) with the line-resident passes and with the
+    per-operator partition passes (WD_LINE2D_OFF=1)."""
+    mk = {"cyl16x257x512": lambda: W.stack([W.cylinder(257, 512, 1.03, r_wall=0.5 * (1 + 0.01 * k)) for k in range(16)]),
+          "ellipse513x1024": lambda: W.ellipse(513, 1024, 1.7),
+          "ellipse1025x2048": lambda: W.ellipse(1025, 2048, 3.1),
+          "channel512x257": lambda: W.channel(512, 257)}[gname]
+    spec = mk()
+    curv = 1 if gname.startswith("cyl") else 0
+    p = wd.default_params(wd.C6, equation=wd.HJ_LAD, curvature=curv, alpha_f=0.495 if curv else 0.49)
+    r = _start(spec)
+    phi0 = W.random_field(spec, 4) * 0.05 * np.minimum(r, 1.0) + r
+    out = {}
+    for off in ("0", "1"):
+        monkeypatch.setenv("WD_LINE2D_OFF", off)
+        g = wd.Grid(spec, prec, wd.C6)
+        a, sa = g.steps(p, g.as_field(phi0), 3, kind=0)
+        b, _ = g.steps(p, g.as_field(phi0), 2, kind=1)
+        out[off] = (to_np(a), to_np(b), sa["res_l2"])
+        g.close()
+    tol = 1e-11 if prec == 0 else 2e-5
+    for x, y in zip(out["0"][:2], out["1"][:2]):
+        np.testing.assert_allclose(x, y, atol=tol * scale(y), rtol=0)
+    assert out["0"][2] == pytest.approx(out["1"][2], rel=1e-8 if prec == 0 else 1e-3)
