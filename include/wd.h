@@ -263,12 +263,15 @@ wd_status wd_change_norms_noalloc(const void* new_dev, const void* old_dev,
                                   double scale, double* norms_dev, void* cuda_stream);
 
 /* Launch shapes chosen by the autotuner for this grid (0: not tuned, the default shape):
- * the block size of the pointwise stage kernel of the fused 2-D path and the block rows of
- * the Cartesian stencil kernels.  Before a grid's first pseudo step the library times the
- * candidate shapes (128 / 256 / 512 threads; 4 / 8 / 16 rows of 32) on the grid's own arrays
- * and keeps the fastest, cached per grid shape for the process; the shapes do not change
- * results.  The environment variable WD_AUTOTUNE=0 disables it. */
-wd_status wd_get_tuning(wd_grid g, int* stage_threads, int* stencil_rows);
+ * the block size of the pointwise stage kernel of the fused 2-D path, the block rows of the
+ * Cartesian stencil kernels, and the number of parts (1, 2 or 4) a stack of 2-D grids on the
+ * line-resident path is split into, each part's launches running on its own stream so that
+ * they fill each other's last waves.  Before a grid's first pseudo step the library times the
+ * candidates (128 / 256 / 512 threads; 4 / 8 / 16 rows of 32; 1 / 2 / 4 parts) on the grid's
+ * own arrays and keeps the fastest, cached per grid shape for the process; none of them
+ * changes any result.  The environment variable WD_AUTOTUNE=0 disables it.  Any pointer may
+ * be NULL.  Errors: WD_ERR_INVALID_ARG for a NULL grid. */
+wd_status wd_get_tuning(wd_grid g, int* stage_threads, int* stencil_rows, int* batch_parts);
 
 /* ---- geometry reuse ---------------------------------------------------------------- */
 

@@ -61,6 +61,11 @@ struct wd_grid_s {
     cudaStream_t stream = nullptr;       // library-owned non-blocking stream (all work)
     cudaStream_t user_stream = nullptr;  // the caller's stream
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    // stacked grids: extra streams for the parts of a batch that run side by side, and the
+    // events that fork them from and join them to `stream`
+    static const int NPART = 4;
+    cudaStream_t pst[NPART - 1] = {};
+    cudaEvent_t ev_fork = nullptr, ev_join[NPART - 1] = {};
     int es = 8;                 // bytes per state element
     size_t bytes = 0;
     double* xyz = nullptr;      // 3 padded coordinate arrays
@@ -96,6 +101,7 @@ struct wd_grid_s {
     int tuned = 0;              // autotuner ran for this grid
     int tune_stage_threads = 0; // chosen block size of the 2-D stage kernel (0: default)
     int tune_by = 0;            // chosen block rows of the Cartesian stencil kernels (0: default)
+    int tune_parts = 0;         // chosen number of parts of a stacked batch (line-resident path)
     int cart = 0;               // uniform Cartesian 3-D grid (diagonal constant metrics)
     double h[3] = {0, 0, 0};    // its spacings
     HostLineTab dtab[3], ftab[3], etab[3];
@@ -296,6 +302,11 @@ static void release(wd_grid g)
     if (g->lsx) cudaGraphExecDestroy(g->lsx);
     if (g->ev_in) cudaEventDestroy(g->ev_in);
     if (g->ev_out) cudaEventDestroy(g->ev_out);
+    if (g->ev_fork) cudaEventDestroy(g->ev_fork);
+    for (int k = 0; k < wd_grid_s::NPART - 1; k++) {
+        if (g->ev_join[k]) cudaEventDestroy(g->ev_join[k]);
+        if (g->pst[k]) cudaStreamDestroy(g->pst[k]);
+    }
     if (g->stream) cudaStreamDestroy(g->stream);
     delete g;
 }
@@ -708,20 +719,36 @@ struct Solver {
         a.equation = p->equation;
         a.lad = p->equation == WD_HJ_LAD && !poisson;
         a.poisson = poisson;
+        a.filter = p->filter;
+        if (p->filter) {
+            LineOp op;
+            if (op_filter(p->alpha_f, op) != WD_OK) a.filter = 0;
+            for (int hw = 1; hw <= 5; hw++)
+                for (int m = 1; m <= hw; m++) a.cf[hw][m] = T(0.5 * op.fa[hw][m] - (m == 1 ? p->alpha_f : 0.0));
+        }
+        a.phin_w = W(W_PHIN);
+        a.partial = g->partial;
+        a.counter = g->counter;
+        a.result = g->result;
+        a.max_partials = g->npartial;
+        a.batch = g->batch;
         return a;
     }
 
-    // Y0, four (X, Y) stage pairs, the direction-0 filter, the direction-1 filter with the
-    // BCs, change norms and commit
-    wd_status step_line2d(F2Args<T, M>& f, bool poisson)
+    // Y0, four (X, Y) stage pairs, the direction-0 filter (FX), the direction-1 filter with the
+    // BCs, change norms and commit (FY): 10 launches.  A stacked batch may run as `parts`
+    // contiguous ranges of its grids, each on its own stream (forked from and joined to the
+    // grid's stream, so a CUDA graph capture records them as parallel branches): the grids are
+    // independent, and the launches of one part fill the partly empty last wave of another's.
+    // Every node and every per-grid norm is computed identically for any number of parts.
+    wd_status line2d_seq(L2Args<T, M> a, bool poisson, cudaStream_t s0)
     {
-        L2Args<T, M> a = l2_args(poisson);
         const PartTab<T> t0 = g->dtab[0].template pview<T>(), t1 = g->dtab[1].template pview<T>();
         const int nf = p->curvature && !poisson ? 4 : 2;
         a.src = W(W_PHIN);
         {
             ProfScope ps(g, WD_K_DERIV);
-            CK(l2_launch<T, M>(a, t1, L2_Y0, nf, st));
+            CK(l2_launch<T, M>(a, t1, L2_Y0, nf, s0));
         }
         for (int s = 0; s < 4; s++) {
             a.src = stage_src(s);
@@ -730,21 +757,55 @@ struct Solver {
             a.next = s < 3;
             {
                 ProfScope ps(g, WD_K_LINE0);
-                CK(l2_launch<T, M>(a, t0, L2_X, nf, st));
+                CK(l2_launch<T, M>(a, t0, L2_X, nf, s0));
             }
             {
                 ProfScope ps(g, WD_K_LINE1);
-                CK(l2_launch<T, M>(a, t1, L2_Y, nf, st));
+                CK(l2_launch<T, M>(a, t1, L2_Y, nf, s0));
             }
         }
-        f.src = stage_dst(3);
-        f.dst = stage_dst(3);
+        a.src = stage_dst(3);
+        a.dst = stage_dst(3);
         if (p->filter) {
             ProfScope ps(g, WD_K_FILTER);
-            CK(p2_launch<T, M>(f, g->ftab[0].template pview<T>(), P2_FILTER0, 0, st));
+            CK(l2_launch<T, M>(a, g->ftab[0].template pview<T>(), L2_FX, nf, s0));
         }
         ProfScope ps(g, WD_K_NORM);
-        CK(p2_launch<T, M>(f, g->ftab[1].template pview<T>(), F2_FILTER, 1, st));
+        CK(l2_launch<T, M>(a, p->filter ? g->ftab[1].template pview<T>() : t1, L2_FY, nf, s0));
+        return WD_OK;
+    }
+
+    // parts of a stacked batch: WD_BATCH_PARTS (1..4) when set, else the autotuner's choice;
+    // one under the kernel timer, which times the grid's own stream only
+    int line2d_parts() const
+    {
+        if (g->prof_on || g->batch < 2 || !g->ev_fork) return 1;
+        int n = g->tune_parts > 0 ? g->tune_parts : 1;
+        if (const char* e = std::getenv("WD_BATCH_PARTS")) n = std::atoi(e);
+        return std::max(1, std::min(n, std::min(g->batch, (int)wd_grid_s::NPART)));
+    }
+
+    wd_status step_line2d(bool poisson, int parts)
+    {
+        L2Args<T, M> a = l2_args(poisson);
+        if (parts <= 1) {
+            a.kbeg = 0;
+            a.kcnt = g->batch;
+            a.counter = g->counter;
+            return line2d_seq(a, poisson, st);
+        }
+        CK(cudaEventRecord(g->ev_fork, st));
+        for (int k = 1; k < parts; k++) CK(cudaStreamWaitEvent(g->pst[k - 1], g->ev_fork, 0));
+        for (int k = 0; k < parts; k++) {
+            a.kbeg = k * g->batch / parts;
+            a.kcnt = (k + 1) * g->batch / parts - a.kbeg;
+            a.counter = g->counter + k;
+            ST(line2d_seq(a, poisson, k == 0 ? st : g->pst[k - 1]));
+        }
+        for (int k = 1; k < parts; k++) {
+            CK(cudaEventRecord(g->ev_join[k - 1], g->pst[k - 1]));
+            CK(cudaStreamWaitEvent(st, g->ev_join[k - 1], 0));
+        }
         return WD_OK;
     }
 
@@ -806,7 +867,7 @@ struct Solver {
             ST(op_filter(p->alpha_f, op));
             std::memcpy(a.fa, op.fa, sizeof(a.fa));
         }
-        if (line2d(a, poisson)) return step_line2d(a, poisson);
+        if (line2d(a, poisson)) return step_line2d(poisson, line2d_parts());
         if (part2d(a)) return step_part2d(a);
         for (int s = 0; s < 4; s++) {
             a.src = stage_src(s);
@@ -1111,6 +1172,20 @@ struct Solver {
         std::snprintf(key, sizeof(key), "%d:%dx%dx%d:p%d:s%d:e%d:c%d:%s", D.ndim, D.n[0], D.n[1], D.n[2],
                       g->desc.precision, g->desc.scheme, p->equation, p->curvature,
                       fused2d() ? "f2" : (cart3d() ? "c3" : "gen"));
+        if (fused2d() && g->batch > 1 && g->ev_fork) {
+            if (p->filter) ST(ensure_filter(p->alpha_f));
+            if (p->equation == WD_HJ_LAD) ST(ensure_lads(p->lad_exp));
+            F2Args<T, M> f = f2_args(false);
+            if (line2d(f, false)) {
+                // parts of the batch: one pseudo step's worth of the passes of stage 0 (they
+                // overwrite their outputs; the first real step recomputes them from phi^n)
+                std::string k2 = std::string(key) + ":l2parts";
+                g->tune_parts = tune_choice(k2, {1, 2, 4}, [&](int c) {
+                    if (c > g->batch) return 1e30f;
+                    return time_calls(st, [&] { step_line2d(false, c); });
+                });
+            }
+        }
         if (fused2d()) {
             if (p->equation == WD_HJ_LAD) ST(ensure_lads(p->lad_exp));
             F2Args<T, M> a = f2_args(false);
@@ -1466,9 +1541,9 @@ static wd_status alloc_impl(wd_grid g)
     g->nred = (int)std::min<long long>((tot + 255) / 256, 1024);
     g->npartial = std::max(g->nred, D.n[0] * D.n[2]);
     ST(dmalloc(g, (void**)&g->partial, (size_t)g->npartial * 2 * 8));
-    ST(dmalloc(g, (void**)&g->counter, sizeof(unsigned)));
+    ST(dmalloc(g, (void**)&g->counter, wd_grid_s::NPART * sizeof(unsigned)));
     ST(dmalloc(g, (void**)&g->result, (size_t)2 * g->batch * 8));
-    CK(cudaMemsetAsync(g->counter, 0, (size_t)sizeof(unsigned), st));
+    CK(cudaMemsetAsync(g->counter, 0, (size_t)wd_grid_s::NPART * sizeof(unsigned), st));
     CK(cudaMemsetAsync(g->result, 0, (size_t)2 * g->batch * 8, st));
     if (cudaMallocHost(&g->hres, (size_t)2 * g->batch * sizeof(double)) != cudaSuccess)
         return set_error(WD_ERR_OOM, "pinned");
@@ -1680,6 +1755,17 @@ wd_status wd_create_grid(const wd_grid_desc* desc, const double* xyz_host, const
         cudaError_t e = cudaGetLastError();
         release(g);
         return cuda_error(e, "stream / event creation");
+    }
+    if (desc->ndim == 2 && desc->n[2] > 1) {
+        bool ok = cudaEventCreateWithFlags(&g->ev_fork, cudaEventDisableTiming) == cudaSuccess;
+        for (int k = 0; ok && k < wd_grid_s::NPART - 1; k++)
+            ok = cudaStreamCreateWithFlags(&g->pst[k], cudaStreamNonBlocking) == cudaSuccess &&
+                 cudaEventCreateWithFlags(&g->ev_join[k], cudaEventDisableTiming) == cudaSuccess;
+        if (!ok) {
+            cudaError_t e = cudaGetLastError();
+            release(g);
+            return cuda_error(e, "stream / event creation");
+        }
     }
     g->es = desc->precision == WD_FP64 ? 8 : 4;
     Dims& D = g->D;
@@ -1986,11 +2072,12 @@ wd_status wd_level_length(wd_grid g, const void* phi_dev, double level, double* 
     return WD_OK;
 }
 
-wd_status wd_get_tuning(wd_grid g, int* stage_threads, int* stencil_rows)
+wd_status wd_get_tuning(wd_grid g, int* stage_threads, int* stencil_rows, int* batch_parts)
 {
-    if (!g) return set_error(WD_ERR_INVALID_ARG, "grid is NULL");
+    if (!g) return set_error(WD_ERR_INVALID_ARG, "NULL grid");
     if (stage_threads) *stage_threads = g->tune_stage_threads;
     if (stencil_rows) *stencil_rows = g->tune_by;
+    if (batch_parts) *batch_parts = g->tune_parts;
     return WD_OK;
 }
 

@@ -6,7 +6,7 @@
 
 namespace wd {
 
-enum { L2_Y0 = 0, L2_X = 1, L2_Y = 2 };
+enum { L2_Y0 = 0, L2_X = 1, L2_Y = 2, L2_FX = 3, L2_FY = 4 };
 
 template <typename T, typename M>
 struct L2Args {
@@ -34,10 +34,26 @@ struct L2Args {
     double eps, cfl, C_lad, eps0;
     int equation, lad, poisson, stage;
     int next;                            // Y: also D_1 and s_1 d4_1 of the stage output
+    // filter passes (Eq. 21): FX filters src along direction 0 into dst; FY filters src along
+    // direction 1, applies the line boundary conditions, commits the new state to phin_w and
+    // reduces the change norms of every stacked grid into result (2 per grid: sum of squares,
+    // max |change|), through per-block partial sums and a fixed-order final reduction
+    T cf[6][6];                          // a_m / 2 - alpha_f [m == 1] of the order-2hw member
+    int filter;                          // 0: FY only applies the BCs and commits
+    T* phin_w;
+    double* partial;
+    unsigned* counter;                   // zero between launches (the last block resets it)
+    double* result;
+    int max_partials;                    // capacity of partial (blocks)
+    int batch;
+    // the stacked grids kbeg .. kbeg + kcnt - 1 of this launch (a contiguous range of lines in
+    // both directions); the parts of a batch run as independent launches on separate streams
+    int kbeg, kcnt;
 };
 
-// one launch of pass `which` (L2_Y0, L2_X or L2_Y) with the partition table of its line
-// direction; nf = 4 with the curvature correction (U and n), else 2
+// one launch of pass `which` (L2_Y0, L2_X, L2_Y, L2_FX or L2_FY) with the partition table of
+// its line direction (the filter table for L2_FX / L2_FY); nf = 4 with the curvature correction
+// (U and n), else 2
 template <typename T, typename M>
 cudaError_t l2_launch(const L2Args<T, M>& a, const PartTab<T>& tb, int which, int nf, cudaStream_t st);
 // whether both directions have partition tables, n0 is a multiple of the vector row segment,

@@ -90,7 +90,7 @@ SIGNATURES = {
     "wd_profile_read": (_i, [_vp, _i, C.POINTER(C.c_double), C.POINTER(C.c_longlong)]),
     "wd_change_norms_noalloc": (_i, [_vp, _vp, _vp, C.c_longlong, _i, _d, _vp, _vp]),
     "wd_reset_geometry": (_i, [_vp, _vp, _vp, _vp]),
-    "wd_get_tuning": (_i, [_vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+    "wd_get_tuning": (_i, [_vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "wd_recede": (_i, [_vp, _vp, _d, _d, _vp, _vp]),
     "wd_level_length": (_i, [_vp, _vp, _d, C.POINTER(C.c_double)]),
     "wd_levelset": (_i, [_vp, _vp, _d, _d, _i]),
@@ -224,10 +224,11 @@ class Grid:
             pass
 
     def tuning(self):
-        """(stage kernel block size, stencil block rows) chosen by the autotuner (0: default)."""
-        a, b = C.c_int(), C.c_int()
-        _check(lib().wd_get_tuning(self._h, C.byref(a), C.byref(b)))
-        return a.value, b.value
+        """(stage kernel block size, stencil block rows, batch parts) chosen by the autotuner
+        (0: default)."""
+        a, b, c = C.c_int(), C.c_int(), C.c_int()
+        _check(lib().wd_get_tuning(self._h, C.byref(a), C.byref(b), C.byref(c)))
+        return a.value, b.value, c.value
 
     def reset_geometry(self, spec):
         """New coordinates / Dirichlet set of the same shape (wd_reset_geometry)."""

@@ -399,14 +399,15 @@ def test_cartesian_2d_steps_with_neumann_faces(wd, oracle, generic, eq, monkeypa
     np.testing.assert_allclose(to_np(outp), refp, atol=1e-10 * scale(refp), rtol=0)
 
 
-@pytest.mark.parametrize("case", ["cylinder", "duct", "star"])
+@pytest.mark.parametrize("case", ["cylinder", "duct", "star", "stack4"])
 def test_autotuned_shapes_do_not_change_results(wd, monkeypatch, case):
-    """The autotuner only picks launch shapes: solves with and without it are bit-identical,
-    and the chosen shapes are among the candidates."""
+    """The autotuner only picks launch shapes and the split of a stacked batch into parts:
+    solves with and without it are bit-identical, and the choices are among the candidates."""
     spec, scheme, prec, kw = {
         "cylinder": (W.cylinder(65, 128, 1.1), 4, 1, dict(equation=1, curvature=1)),
         "duct": (W.duct(32, nx=16), 2, 1, dict(equation=1)),
         "star": (W.star(97), 1, 1, dict(equation=1, lad_exp=4.0, eps=0.15)),
+        "stack4": (W.stack(_cyl_batch([0.5, 0.45, 0.55, 0.6], nr=65, nt=128)), 4, 1, dict(equation=1, curvature=1)),
     }[case]
     p = wd.default_params(scheme, tol_l2=1e-6, max_iters=400, **kw)
     out = {}
@@ -418,12 +419,31 @@ def test_autotuned_shapes_do_not_change_results(wd, monkeypatch, case):
         g.close()
     np.testing.assert_array_equal(out["0"][0], out["1"][0])
     assert out["0"][1] == out["1"][1]
-    assert out["0"][2] == (0, 0)
-    threads, rows = out["1"][2]
-    if case == "cylinder":
+    assert out["0"][2] == (0, 0, 0)
+    threads, rows, parts = out["1"][2]
+    if case in ("cylinder", "stack4"):
         assert threads in (128, 256, 512)
     else:
         assert rows in (4, 8, 16)
+    if case == "stack4":
+        assert parts in (1, 2, 4)
+
+
+def test_batch_parts_are_bit_identical(wd, monkeypatch):
+    """A stack of 2-D grids on the line-resident path split into 1, 2 or 4 parts (each part's
+    launches on its own stream) gives bit-identical fields, norms and iteration counts."""
+    spec = W.stack(_cyl_batch([0.5, 0.45, 0.55, 0.6, 0.52], nr=65, nt=128))
+    p = wd.default_params(4, equation=1, curvature=1, tol_l2=1e-6, max_iters=400)
+    out = {}
+    for parts in ("1", "2", "4"):
+        monkeypatch.setenv("WD_BATCH_PARTS", parts)
+        g = wd.Grid(spec, wd.FP32_METRIC64, 4)
+        phi, st = g.solve(p)
+        out[parts] = (to_np(phi), st["iters"], st["res_l2"])
+        g.close()
+    for k in ("2", "4"):
+        np.testing.assert_array_equal(out[k][0], out["1"][0])
+        assert out[k][1:] == out["1"][1:]
 
 
 @pytest.mark.parametrize("scheme,prec,tol", [(1, 0, 1e-6), (4, 0, 1e-6), (1, 1, 2e-4)])
