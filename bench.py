@@ -113,33 +113,36 @@ def peak_hbm():
         return 6800.0, "fallback"
 
 
-# DRAM bytes (read + write) per launch of the kernel classes of this workload, from one ncu
-# capture of the current kernels (k_p2_div2, both directions in one launch: 54.8 MB read +
-# 14.2 MB written, against 84.2 MB of algorithmic bytes; the other divergence parts are
-# still in L2 when the launch ends).
-PROFILED_TRAFFIC = {"div": 68.97e6}
+# DRAM bytes (read + write) per launch of the dominant kernel class, from one ncu capture of
+# the current kernel on this workload (profiles/k_l2_passes_cylinder_batch16.md): k_l2_y, the
+# direction-1 pass of an RK stage, stage 2 (120.2 MB read + 14.2 MB written).
+PROFILED_TRAFFIC = {"line1": 134.36e6}
 
 
 def algorithmic_bytes(cls, nodes, nd, es, ms, curv, lad=True):
-    """Algorithmic DRAM bytes of one launch of a kernel class of the fused 2-D step (every
-    array a pass must touch read once, every output written once; one launch = one grid
-    direction for the line passes):
-      deriv  phi in, d(phi)/dxi_l out; LAD: s_l in and, for direction 1, s_1 d4_1(phi)
-             out; direction 0 (half of the launches) reads it back and writes the smoothed
-             C|LAD| instead
-      div    one launch does both directions (k_p2_div2): D_0, D_1 and the 4 metric arrays
-             of U in, once; each direction's divergence part(s) out
-      point  stage kernel (LAD + curvature): 11 state-size arrays in (Lap_0, Lap_1,
-             kappa_0, kappa_1, D_0, D_1, phi_s, G_0, phi^n, acc, dt) and the 4 metric arrays
-             of U, the stage value and the RK4 accumulator out, plus the Dirichlet flags
-      filter / norm: the field in and out (norm: plus the old state and the flags)"""
+    """Algorithmic DRAM bytes of one launch of a kernel class of the line-resident 2-D step
+    (every array a launch must touch read once, every output written once), averaged over
+    the four RK stages where they differ:
+      deriv  Y0: phi and s_1 in; D_1 and s_1 d4_1(phi) out
+      line0  direction-0 pass: phi, D_1, s_1 d4_1, s_0 and the 4 metric arrays of U in; D_0,
+             the direction-0 Laplacian part, the smoothed C|LAD| (and the direction-0
+             curvature part) out
+      line1  direction-1 pass: D_0, D_1, the 4 metric arrays, smoothed C|LAD|, Laplacian (and
+             curvature) part, phi_s, phi^n, the Dirichlet flags in; stage 0 the two metric
+             sums of the time step, stages 1-3 dt and acc; stages 0-2 s_1.  Out: the stage
+             value; acc (stages 0-2), dt (stage 0), D_1 and s_1 d4_1 (stages 0-2)
+      filter FX: the field in and out
+      norm   FY: the field, phi^n and the flags in; phi^n out"""
+    lad_f = 1 if lad else 0
+    kap = 1 if curv else 0
     if cls == "deriv":
-        return int(nodes * (2 * es + ((1.5 * es + ms) if lad else 0)))
-    if cls == "div":
-        nout = 2 if curv else 1
-        return int(nodes * (2 * es + 4 * ms + 2 * nout * es))
-    if cls == "point":
-        return nodes * (13 * es + 4 * ms + 1)
+        return int(nodes * (es + lad_f * ms + es + lad_f * es))
+    if cls == "line0":
+        return int(nodes * ((2 + lad_f) * es + (lad_f + 4) * ms + (2 + lad_f + kap) * es))
+    if cls == "line1":
+        reads = (2 + 4 + lad_f + 1 + kap + 2) * es + 0.25 * 2 * ms + 0.75 * 2 * es + 0.75 * lad_f * ms
+        writes = (1 + 0.75 + 0.25 + 0.75 * (1 + lad_f)) * es
+        return int(nodes * (reads + writes + 1))
     if cls == "filter":
         return nodes * 2 * es
     if cls == "norm":
@@ -183,7 +186,7 @@ def square_report(wd):
     err = float(np.abs(phi.cpu().numpy() - np.minimum.reduce([x, 1 - x, y, 1 - y])).max())
     g.close()
     return {"nodes": sp.N, "time_to_converged_s": round(ts, 4), "iters": st["iters"] + st["poisson_iters"],
-            "res_l2": st["res_l2"], "max_err_vs_exact": err}
+            "max_err_vs_exact": float("%.3g" % err)}
 
 
 def run_native(args, rank, world):
@@ -254,7 +257,8 @@ def run_native(args, rank, world):
     ms, cell_iters = reduce_over_ranks(total_ms_plain, nodes * (iters + piters), world, "cuda")
     value = cell_iters / (ms * 1e-3) / 1e6
 
-    # accuracy of the timed result against the exact distance r - r_wall of every cylinder
+    # accuracy of the timed result against the FP64 oracle (the stored oracle solutions of the
+    # 16 cylinders, tests/golden, written by the oracle alone) and the exact r - r_wall
     import numpy as np
 
     n1 = single.N
@@ -262,6 +266,9 @@ def run_native(args, rank, world):
     exact = np.hypot(*spec.xyz) - rw
     phi_np = phi.double().cpu().numpy()
     err32 = float(np.abs(phi_np - exact).max())
+    gold = json.load(open(os.path.join(ROOT, "tests", "golden", "cylinder257x512_c6_lad_curv.json")))["members"]
+    d_oracle = np.concatenate([np.repeat(np.asarray(m["d"]), 512) for m in gold[:BATCH]])
+    err32_oracle = float(np.abs(phi_np - d_oracle).max())
 
     # FP64 plain form on one cylinder (r_wall 0.5): time-to-converged at tolerance 1e-10
     g64 = wd.Grid(single, wd.FP64, wd.C6, stream=stream)
@@ -276,6 +283,7 @@ def run_native(args, rank, world):
     torch.cuda.synchronize()
     t64 = ev0.elapsed_time(ev1) * 1e-3
     err64 = float(np.abs(phi64.cpu().numpy() - exact[:n1]).max())
+    err64_oracle = float(np.abs(phi64.cpu().numpy() - d_oracle[:n1]).max())
     diff = float(np.abs(phi64.cpu().numpy() - phi_np[:n1]).max())
     del g64
 
@@ -308,7 +316,11 @@ def run_native(args, rank, world):
                 "avg_launch_us": round(kms / kn * 1e3, 3),
                 "frac_of_nominal_7900": round(ach / 7900.0, 4),
                 "share_of_timed": round(kms / max(1e-9, sum(v[0] for v in prof.values())), 3)}
-    launches = sum(v[1] for v in prof.values())
+    # launches of the timed solves: the profiled solves run the batch as one part; the timed
+    # ones split the line-resident passes into the autotuned number of parts
+    parts = max(1, g.tuning()[2])
+    split = ("deriv", "line0", "line1", "filter", "norm")
+    launches = sum(v[1] * (parts if k in split else 1) for k, v in prof.items())
 
     out = {
         "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world,
@@ -320,12 +332,7 @@ def run_native(args, rank, world):
                                "FP32 state and loop, metric Jacobians computed in FP64, tol RMS 1e-6 per cylinder, Poisson 100",
                    "batch": BATCH, "nodes": nodes, "pseudo_steps_per_solve": (iters + piters) / args.steps,
                    "l2_between_steps": "flushed (256 MB write)",
-                   "parallelism": f"replicas x{world}"},
-        "time_to_converged_s": {"fp32_batched_per_cylinder": round(ms / args.steps * 1e-3 / BATCH, 4),
-                                "fp32_batch_of_%d" % BATCH: round(ms / args.steps * 1e-3, 4),
-                                "fp64_plain_one_cylinder": round(t64, 4), "fp64_iters": st64["iters"]},
-        "accuracy": {"max_err_vs_exact_fp32m64": err32, "max_err_vs_exact_fp64": err64,
-                     "max_fp32_minus_fp64": diff},
+                   "parallelism": f"replicas x{world}", "batch_parts": parts},
         "roofline": roof,
         "kernel_ms": {k: round(v[0], 3) for k, v in prof.items()},
         "gpu_launches": int(launches),
@@ -334,18 +341,31 @@ def run_native(args, rank, world):
                 "h2d_bytes_per_step": int(spec.xyz.nbytes), "d2h_bytes_per_step": int(nodes * 4),
                 "what": "wd_create_grid from host coordinates + wd_solve into pinned host memory + destroy"},
     }
+    tail = {
+        "time_to_converged_s": {"fp32_batch_of_%d" % BATCH: round(ms / args.steps * 1e-3, 4),
+                                "fp32_batched_per_cylinder": round(ms / args.steps * 1e-3 / BATCH, 4),
+                                "fp64_plain_one_cylinder": round(t64, 4), "fp64_iters": st64["iters"],
+                                "fp32_iters": round((iters + piters) / args.steps, 1)},
+        "accuracy": {"max_abs_vs_fp64_oracle": {"fp32_batch": float("%.3g" % err32_oracle),
+                                                "fp64_plain": float("%.3g" % err64_oracle),
+                                                "bar": {"fp32": 2e-4, "fp64": 1e-6}},
+                     "max_abs_vs_exact": {"fp32_batch": float("%.3g" % err32), "fp64_plain": float("%.3g" % err64)},
+                     "max_fp32_minus_fp64": float("%.3g" % diff),
+                     "oracle": "FP64 CPU oracle solved to RMS 1e-12 (tests/golden/cylinder257x512_c6_lad_curv.json)"},
+    }
     if rank == 0:
         if not args.no_extras:
             out["serving"] = serving_report(wd, args.full)
             out["star_burn"] = star_report(wd, args.full)
             d = duct_report(wd)
             peak_hbm_gbs = peak_hbm()[0]
-            d["frac_of_fused_roofline"] = round(d["mcell_iter_s"] * 1e6 * 112 / (peak_hbm_gbs * 1e9), 4)
+            d["frac_of_112B_roofline"] = round(d["mcell_iter_s"] * 1e6 * 112 / (peak_hbm_gbs * 1e9), 4)
             out["duct"] = d
             out["square65"] = square_report(wd)
             out["upwind_vs_central"] = upwind_report(wd)
             out["levelset_regression"] = levelset_report(wd)
         out["cpu_baseline"] = cpu_baseline()
+        out.update(tail)
         print(json.dumps(out), flush=True)
     if world > 1:
         import torch.distributed as dist
@@ -356,13 +376,13 @@ def run_native(args, rank, world):
 def serving_report(wd, full):
     """Ellipse stream through the request loop (wd_server_*): the closed-loop saturation rate
     of the request mix, then Poisson arrivals at 0.7 x that rate; p50 / p99 latency from
-    submission to completion, throughput.  Default: 12 requests (full: 1000)."""
+    submission to completion, throughput.  Default: 24 requests (full: 1000)."""
     import numpy as np
     import torch
 
     from paper_2111_09859_gb300 import workloads as W
 
-    n = 1000 if full else 12
+    n = 1000 if full else 24
     shapes = W.ellipse_stream(n)
     specs = [W.ellipse(*sh) for sh in shapes]
     p = wd.default_params(wd.C6, equation=wd.HJ_LAD, tol_l2=1e-6, max_iters=20000)
@@ -393,27 +413,24 @@ def serving_report(wd, full):
     rate = 0.7 * rate_sat
     arr = W.poisson_arrivals(n, rate, seed=2111)
     span2, lat2, cells2, info2 = run(arr)
-    return {"requests": n, "sizes": "ellipse O-grids 65x128 .. 1025x2048, AR U[1,4], seeds 9859 / 2111",
-            "precision": "FP32 (metrics computed in FP64), C6 + LAD, tol 1e-6",
-            "saturation_req_s": round(rate_sat, 3), "arrival_rate_req_s": round(rate, 3),
-            "p50_latency_s": round(float(np.percentile(lat2, 50)), 4),
-            "p99_latency_s": round(float(np.percentile(lat2, 99)), 4),
-            "throughput_req_s": round(n / span2, 3), "mcell_iter_s": round(cells2 / span2 / 1e6, 1),
-            "peak_concurrent": info2["peak_running"],
-            "closed_loop_p50_p99_s": [round(float(np.percentile(lat, 50)), 4), round(float(np.percentile(lat, 99)), 4)]}
+    return {"requests": n, "sizes": "ellipse 65x128..1025x2048, AR U[1,4]", "fp": "FP32 (FP64 metrics), C6+LAD, tol 1e-6",
+            "sat_req_s": round(rate_sat, 3), "rate_req_s": round(rate, 3),
+            "p50_s": round(float(np.percentile(lat2, 50)), 3), "p99_s": round(float(np.percentile(lat2, 99)), 3),
+            "req_s": round(n / span2, 3), "mcell_iter_s": round(cells2 / span2 / 1e6, 1),
+            "peak_concurrent": info2["peak_running"]}
 
 
 def star_report(wd, full):
     """Receding star grain: 1025^2 box, E4 + LAD (Delta x^4 scale), eps 0.15, alpha_f 0.45,
     FP32; the surface recedes by 0.002 per step, each step a warm re-solve on a session grid
-    through the request loop.  Default 50 steps (full: 200).  The burning perimeter of the
+    through the request loop.  Default 100 steps (full: 200).  The burning perimeter of the
     computed zero level against the marching-squares length of the exact offset field."""
     import numpy as np
     import torch
 
     from paper_2111_09859_gb300 import workloads as W
 
-    steps = 200 if full else 50
+    steps = 200 if full else 100
     sp = W.star(1025)
     h, sd = sp.meta["h"], sp.meta["signed_distance"]
     g = wd.Grid(sp, wd.FP32_METRIC64, wd.E4)
@@ -439,11 +456,9 @@ def star_report(wd, full):
     err = float(np.abs(a - ex)[sel].max())
     srv.close()
     g.close()
-    return {"steps": steps, "grid": "1025x1025 on [-1,1]^2", "initial_solve_s": round(lat0, 4),
-            "initial_iters": st0["iters"], "step_p50_s": round(float(np.percentile(lats, 50)), 4),
-            "step_p99_s": round(float(np.percentile(lats, 99)), 4),
+    return {"steps": steps, "grid": "1025^2", "first_solve_s": round(lat0, 3), "first_iters": st0["iters"],
+            "step_p50_s": round(float(np.percentile(lats, 50)), 4), "step_p99_s": round(float(np.percentile(lats, 99)), 4),
             "warm_iters_median": int(np.median(its)), "total_s": round(total, 2),
-            "perimeter": round(L, 5), "perimeter_exact_field": round(Lx, 5),
             "perimeter_rel_err": round((L - Lx) / Lx, 5), "max_err_near_port_h": round(err / h, 3)}
 
 
@@ -495,11 +510,12 @@ def upwind_report(wd):
             g.close()
         out[name] = row
     uw = out["UW_std"]["ms_per_100_steps_generic"]
-    out["uw_time_over"] = {k: round(uw / out[k]["ms_per_100_steps_generic"], 3)
-                           for k in ("E2_std", "E4_std", "E4_lad", "C6_lad")}
-    out["uw_time_over_fast_path"] = {k: round(uw / out[k]["ms_per_100_steps_fast"], 3)
-                                     for k in ("E2_std", "E4_std", "E4_lad", "C6_lad")}
-    return out
+    compact = {"grid": "channel 1024x513 FP64", "ms_per_100": {}}
+    for k in ("UW_std", "E2_std", "E4_std", "E4_lad", "C6_lad"):
+        compact["ms_per_100"][k] = [out[k]["ms_per_100_steps_generic"], out[k].get("ms_per_100_steps_fast")]
+    compact["uw_over_fast"] = {k: round(uw / out[k]["ms_per_100_steps_fast"], 2)
+                               for k in ("E2_std", "E4_std", "E4_lad", "C6_lad")}
+    return compact
 
 
 def levelset_report(wd):
@@ -550,16 +566,10 @@ def levelset_report(wd):
     bytes_stage = nodes * 4 * 4.5
     stage_us = ms_step * 1e3 / 4
     g.close()
-    return {"grid": "1025x1025 on [-1,1]^2", "F": F, "t_end": T, "steps": ns, "dt": dt,
-            "init_iters": st["iters"], "ms_per_step": round(ms_step, 4),
-            "mnode_steps_per_s": round(nodes / (ms_step * 1e-3) / 1e6, 1),
-            "stage_us": round(stage_us, 2), "stage_algorithmic_bytes": int(bytes_stage),
-            "stage_gbs": round(bytes_stage / (stage_us * 1e-6) / 1e9, 1),
-            "note": "the march's working set (phi, two stage buffers, acc: 17 MB) stays in the 129 MB L2, "
-                    "so HBM does not bound a stage; about 3 us of each is launch and tail",
-            "perimeter": per,
-            "perimeter_from_exact_d0_at_t_end": {"value": round(L_exact_start, 5),
-                                                 "rel_err": round(L_exact_start / per[-1]["exact"] - 1, 5)}}
+    return {"grid": "star 1025^2", "F": F, "t_end": T, "steps": ns, "ms_per_step": round(ms_step, 4),
+            "stage_us": round(stage_us, 2), "stage_gbs_from_l2": round(bytes_stage / (stage_us * 1e-6) / 1e9, 1),
+            "perimeter_rel_err_t_end": per[-1]["rel_err"],
+            "perimeter_rel_err_from_exact_d0": round(L_exact_start / per[-1]["exact"] - 1, 5)}
 
 
 def duct_report(wd):
@@ -590,11 +600,9 @@ def duct_report(wd):
     ts = time.perf_counter() - t0
     err = float(np.abs(out.double().cpu().numpy() - ex).max())
     g.close()
-    return {"nodes": sp.N, "ms_per_pseudo_step": round(ms, 3), "mcell_iter_s": round(sp.N / (ms * 1e-3) / 1e6, 1),
-            "fused_min_bytes_per_cell_iter": 112,
-            "frac_of_fused_roofline": None,
+    return {"nodes": sp.N, "ms_per_step": round(ms, 3), "mcell_iter_s": round(sp.N / (ms * 1e-3) / 1e6, 1),
             "solve_s": round(ts, 3), "solve_iters": st["iters"] + st["poisson_iters"],
-            "max_err_vs_exact": err}
+            "max_err_vs_exact": float("%.3g" % err)}
 
 
 def cpu_baseline(n_steps=12):
