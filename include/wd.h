@@ -147,7 +147,7 @@ wd_status wd_create_grid(const wd_grid_desc* desc, const double* xyz_host,
                          const uint8_t* mask_host, const double* dval_host,
                          void* cuda_stream, wd_grid* out);
 
-/* Frees every device buffer of the grid (NULL is ignored). */
+/* Frees every device buffer of the grid (NULL is ignored); no counterpart in the paper. */
 void wd_destroy_grid(wd_grid g);
 
 /* Changes the stream used by later calls on g. */
@@ -170,14 +170,25 @@ wd_status wd_solve(wd_grid g, const wd_solve_params* p, void* phi_dev, wd_stats*
 wd_status wd_step_unsteady(wd_grid g, const uint8_t* mask_dev, const void* dval_dev,
                            const wd_solve_params* p, void* phi_dev, wd_stats* stats);
 
-/* Solves n independent grids with the same parameters; phi_dev[i] and stats[i] belong to
- * grids[i].  Returns the first non-OK status (every grid is still attempted). */
+/* Steady solves of Sec. 3.3 (as wd_solve) of n independent grids of any shapes with the same
+ * parameters; phi_dev[i] and stats[i] belong to grids[i].  The solves run as interleaved
+ * resumable tasks on the grids' own streams: each round queues one slice of check_every
+ * pseudo steps of every unfinished solve before waiting for any, so the slices of all grids
+ * run side by side on the GPU.  Each grid gets bit for bit what wd_solve gives it alone.
+ * stats[i].seconds is the wall time of the whole batch.  Returns the first non-OK status in
+ * grid order (every grid is still solved).  Errors: WD_ERR_INVALID_ARG for n < 0, NULL
+ * arrays, a NULL grid or phi, or a grid listed twice. */
 wd_status wd_solve_batch(wd_grid* grids, int n, const wd_solve_params* p, void** phi_dev,
                          wd_stats* stats);
 
-/* Device bytes wd_create_grid would allocate for desc (0 if desc is invalid). */
+/* Device bytes wd_create_grid would allocate for desc (0 if desc is invalid): the node
+ * coordinates and the metric arrays of Sec. 3.1, the RK4 and pseudo-time work fields of
+ * Sec. 3.3, the line-solve tables of Eqs. 16 and 21 (the allocation itself has no
+ * counterpart in the paper).  The request loop admits requests by this footprint. */
 size_t wd_query_footprint(const wd_grid_desc* desc, const wd_solve_params* p);
 
+/* Name of a status code, and a one-line description of the calling thread's most recent
+ * failure (no counterpart in the paper). */
 const char* wd_status_string(wd_status s);
 const char* wd_last_error(void);
 

@@ -11,6 +11,7 @@
 #include <string>
 #include <type_traits>
 #include <map>
+#include <memory>
 #include <mutex>
 #include <vector>
 
@@ -1867,14 +1868,60 @@ wd_status wd_step_unsteady(wd_grid g, const uint8_t* mask_dev, const void* dval_
     return s;
 }
 
+// The solves of wd_solve, run as resumable tasks (Solver::begin .. finish) on the grids' own
+// streams: every round queues one slice (check_every pseudo steps, a CUDA graph, and the copy
+// of its change norms) of each unfinished solve before waiting for any, so the slices of all
+// grids, whatever their shapes, run side by side on the GPU; each grid then gets exactly what
+// wd_solve gives it alone (the same kernels, slices and convergence checks).
 wd_status wd_solve_batch(wd_grid* grids, int n, const wd_solve_params* p, void** phi_dev,
                          wd_stats* stats)
 {
-    if (!grids || !phi_dev || n < 0) return set_error(WD_ERR_INVALID_ARG, "bad batch");
-    wd_status first = WD_OK;
+    if (n < 0 || (n > 0 && (!grids || !phi_dev))) return set_error(WD_ERR_INVALID_ARG, "bad batch");
+    ST(check_params(p));
     for (int i = 0; i < n; i++) {
-        wd_status s = wd_solve(grids[i], p, phi_dev[i], stats ? stats + i : nullptr);
-        if (s != WD_OK && first == WD_OK) first = s;
+        if (!grids[i] || !phi_dev[i]) return set_error(WD_ERR_INVALID_ARG, "NULL grid or phi in the batch");
+        for (int k = 0; k < i; k++)
+            if (grids[k] == grids[i]) return set_error(WD_ERR_INVALID_ARG, "a grid appears twice in the batch");
+    }
+    const auto t0 = std::chrono::steady_clock::now();
+    std::vector<std::unique_ptr<StreamGuard>> guards;
+    std::vector<std::unique_ptr<SolveTask>> tasks;
+    std::vector<wd_status> rc(n, WD_OK);
+    for (int i = 0; i < n; i++) {
+        guards.emplace_back(new StreamGuard(grids[i]));
+        tasks.emplace_back(make_solve_task(grids[i], p));
+        rc[i] = tasks[i]->begin(phi_dev[i], false);
+    }
+    auto live = [&](int i) { return rc[i] == WD_OK && !tasks[i]->finished(); };
+    for (;;) {
+        bool any = false;
+        for (int i = 0; i < n; i++)
+            if (live(i)) {
+                any = true;
+                rc[i] = tasks[i]->enqueue();
+            }
+        if (!any) break;
+        for (int i = 0; i < n; i++) {
+            if (rc[i] != WD_OK || tasks[i]->finished()) continue;
+            if (tasks[i]->check()) {
+                const cudaError_t e = cudaStreamSynchronize(grid_stream(grids[i]));
+                if (e != cudaSuccess) rc[i] = cuda_error(e, "wd_solve_batch");
+            }
+            if (rc[i] == WD_OK) rc[i] = tasks[i]->complete();
+        }
+    }
+    wd_stats dummy;
+    for (int i = 0; i < n; i++) {
+        if (rc[i] == WD_OK || rc[i] == WD_ERR_NOT_CONVERGED || rc[i] == WD_ERR_DIVERGED)
+            rc[i] = tasks[i]->finish(phi_dev[i], stats ? stats + i : &dummy);
+    }
+    wd_status first = WD_OK;
+    const double sec = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    for (int i = 0; i < n; i++) {
+        const cudaError_t e = cudaStreamSynchronize(grid_stream(grids[i]));
+        if (e != cudaSuccess && rc[i] == WD_OK) rc[i] = cuda_error(e, "wd_solve_batch");
+        if (stats) stats[i].seconds = sec;
+        if (rc[i] != WD_OK && first == WD_OK) first = rc[i];
     }
     return first;
 }

@@ -383,6 +383,21 @@ def footprint(spec, precision=FP64, scheme=E4):
     return lib().wd_query_footprint(C.byref(d), None)
 
 
+def solve_batch(grids, params, outs=None):
+    """wd_solve_batch: the solves of every Grid in grids, side by side on the GPU; returns
+    (list of result tensors, list of stats dicts, status).  outs: optional result tensors
+    (one per grid, the grid's precision)."""
+    n = len(grids)
+    outs = [g.empty() for g in grids] if outs is None else list(outs)
+    harr = (C.c_void_p * n)(*[g._h for g in grids])
+    parr = (C.c_void_p * n)(*[o.data_ptr() for o in outs])
+    st = (Stats * n)()
+    s = lib().wd_solve_batch(harr, n, C.byref(params), parr, st)
+    if s not in (OK, ERR_NOT_CONVERGED):
+        _check(s)
+    return outs, [st[i].as_dict() for i in range(n)], s
+
+
 def _noalloc_inputs(new, old, mask, out):
     """Checks the arrays of change_norms_noalloc before anything reaches the library, so
     that a wrong dtype, length or layout can never make the kernel read past an array:

@@ -152,17 +152,21 @@ def test_paper_claims_on_channel(oracle):
 
 
 def test_lad_constant_sensitivity(oracle):
-    """Changing C by 10% changes the LAD error by much less than 10% (the paper reports
-    under 1% on its grids; here the change is a few percent)."""
+    """Changing C by 10% changes the LAD error by a few percent: 3-5% in this reading, where
+    the paper reports under 1% (a stated deviation, tests/golden/paper_claims.json), and far
+    less than the 10% change of C itself."""
+    claim = GOLD["lad_c_sensitivity"]
     sp = W.channel(8, 65)
     y = sp.xyz[1]
     ex = np.minimum(y, 1 - y)
     g = grid_of(oracle, sp, 1)
     e = []
-    for C in (0.09, 0.11):
+    for C in (0.09, 0.10, 0.11):
         phi, _ = g.solve(equation=1, C_lad=C, tol_l2=1e-12, poisson_max_iters=100, poisson_tol=0)
         e.append(np.sqrt(((phi - ex) ** 2).mean()))
-    assert abs(e[1] - e[0]) / e[0] < 0.15
+    for k in (0, 2):
+        assert abs(e[k] - e[1]) / e[1] < claim["rel_change_max_checked"], e
+    assert e[0] < e[1] < e[2]   # more diffusivity, more smoothing of the kink
 
 
 def sampled_ellipse_distance(sp, n=16384):
