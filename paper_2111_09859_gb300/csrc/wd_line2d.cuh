@@ -892,26 +892,38 @@ __global__ void __launch_bounds__(32 * LXShape<T>::W) k_l2_fx(L2Args<T, M> a, Pa
     }
 }
 
-// ---- FY: filter along direction 1, line boundary conditions, commit, change norms ------------
-template <typename T, typename M, int R, int NC>
-__global__ void __launch_bounds__(32 * LYShape<T>::W, ly_minb(R)) k_l2_fy(L2Args<T, M> a, PartTab<T> tb)
+// ---- FY: filter along a strided direction DIR (1, or 2 of a 3-D grid); with a.commit also
+// the line boundary conditions (far-field / Neumann ends of 2-D direction-1 lines, Dirichlet
+// nodes), the commit of the new state and the change norms, else the filtered field into dst
+// Direction-2 lines of a 3-D grid lie a whole plane apart: their blocks take 32 neighbouring
+// lines (128-byte row segments), each warp solving 32 / NW of them.
+template <typename T, int DIR>
+struct LFShape {
+    static constexpr int NW = LYShape<T>::W;                     // warps per block
+    static constexpr int W = DIR == 2 ? 32 : LYShape<T>::W;      // lines per block
+};
+
+template <typename T, typename M, int R, int NC, int DIR>
+__global__ void __launch_bounds__(32 * LFShape<T, DIR>::NW, ly_minb(R)) k_l2_fy(L2Args<T, M> a, PartTab<T> tb)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
-    __shared__ double s_ss[LYShape<T>::W], s_mx[LYShape<T>::W];
+    __shared__ double s_ss[LFShape<T, DIR>::NW], s_mx[LFShape<T, DIR>::NW];
     __shared__ int s_last;
     using L = LL<R>;
-    constexpr int W = LYShape<T>::W, VW = VecT<T>::n, JS = 16 * W;
+    constexpr int W = LFShape<T, DIR>::W, NW = LFShape<T, DIR>::NW, VW = VecT<T>::n;
+    constexpr int TPR = W / VW;                 // threads per row segment
+    constexpr int JS = 32 * NW / TPR;           // rows per sweep
     const Dims& D = a.D;
-    const int N = NC > 0 ? NC : D.n[1], per = NC > 0 ? 0 : D.per[1];
-    const int q0 = a.kbeg * D.n[0] + blockIdx.x * W;
+    const int N = NC > 0 ? NC : D.n[DIR], per = NC > 0 ? 0 : D.per[DIR];
+    const int q0 = (DIR == 1 ? a.kbeg * D.n[0] : 0) + blockIdx.x * W;
     const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
     T* sm = reinterpret_cast<T*>(smraw);
     auto buf = [&](int l) { return sm + (size_t)l * L::NS; };
     T* scr = sm + (size_t)W * L::NS + 16 * w;
-    const long long st = D.pitch;
-    const int lv0 = (tid & 1) * VW;
-    const long long lb = D.line_base(1, q0 + lv0);
-    const int jr = tid >> 1;
+    const long long st = D.stride(DIR);
+    const int lv0 = (tid % TPR) * VW;
+    const long long lb = D.line_base(DIR, q0 + lv0);
+    const int jr = tid / TPR;
     for (int j = jr; j < N; j += JS) {
         T t[VW];
         vldg(a.src + lb + (long long)j * st, t);
@@ -920,25 +932,37 @@ __global__ void __launch_bounds__(32 * LYShape<T>::W, ly_minb(R)) k_l2_fy(L2Args
         for (int u = 0; u < VW; u++) buf(lv0 + u)[s] = t[u];
     }
     __syncthreads();
-    if (a.filter) {
-        T* P = buf(w);
-        if (per) {
-            ghost_fill<R>(P, lane);
+    if (a.filter)
+        for (int l = w; l < W; l += NW) {
+            T* P = buf(l);
+            if (per) {
+                ghost_fill<R>(P, lane);
+                __syncwarp();
+            }
+            T x[R];
+            rows_of<NC, T, R>(x, P, lane, N, per, scr, OpFilter<T>{a.cf});
+            if (tb.implicit) part_solve<T, R>(x, tb, lane);
+            const T* Fb = P + L::lane_base(lane);
+#pragma unroll
+            for (int k = 0; k < R; k++) x[k] += Fb[k];
+            __syncwarp();
+            store_rows<T, R>(P, x, lane);
             __syncwarp();
         }
-        T x[R];
-        rows_of<NC, T, R>(x, P, lane, N, per, scr, OpFilter<T>{a.cf});
-        if (tb.implicit) part_solve<T, R>(x, tb, lane);
-        const T* Fb = P + L::lane_base(lane);
-#pragma unroll
-        for (int k = 0; k < R; k++) x[k] += Fb[k];
-        __syncwarp();
-        store_rows<T, R>(P, x, lane);
-    }
     __syncthreads();
-    // far-field / Neumann end rows are committed by the end threads below
-    const bool ff_lo = !per && (a.bclo1 == WD_BC_FARFIELD || a.bclo1 == WD_BC_NEUMANN);
-    const bool ff_hi = !per && (a.bchi1 == WD_BC_FARFIELD || a.bchi1 == WD_BC_NEUMANN);
+    if (!a.commit) {
+        for (int j = jr; j < N; j += JS) {
+            const int s = L::slot(j);
+            T nv[VW];
+#pragma unroll
+            for (int u = 0; u < VW; u++) nv[u] = buf(lv0 + u)[s];
+            vst(a.dst + lb + (long long)j * st, nv);
+        }
+        return;
+    }
+    // far-field / Neumann end rows (2-D direction-1 lines) are committed by the end threads below
+    const bool ff_lo = DIR == 1 && D.ndim == 2 && !per && (a.bclo1 == WD_BC_FARFIELD || a.bclo1 == WD_BC_NEUMANN);
+    const bool ff_hi = DIR == 1 && D.ndim == 2 && !per && (a.bchi1 == WD_BC_FARFIELD || a.bchi1 == WD_BC_NEUMANN);
     NormAcc<T> acc;
     for (int j = jr; j < N; j += JS) {
         if ((j == 0 && ff_lo) || (j == N - 1 && ff_hi)) continue;
@@ -969,7 +993,7 @@ __global__ void __launch_bounds__(32 * LYShape<T>::W, ly_minb(R)) k_l2_fy(L2Args
                 const long long fi = (long long)(qline / D.n[0]) + (long long)D.n[2] * (qline % D.n[0]);
                 nv = v1 + T((side ? a.ffr_hi : a.ffr_lo)[fi]) * (v1 - v2);
             }
-            const long long e = D.line_base(1, q0 + l) + (long long)(side ? N - 1 : 0) * st;
+            const long long e = D.line_base(DIR, q0 + l) + (long long)(side ? N - 1 : 0) * st;
             const T ov = a.phin[e];
             if (a.mask[e]) nv = a.poisson ? T(0) : __ldg(a.dval + e);
             else acc.add(nv - ov);
@@ -990,7 +1014,7 @@ __global__ void __launch_bounds__(32 * LYShape<T>::W, ly_minb(R)) k_l2_fy(L2Args
     __syncthreads();
     if (tid == 0) {
         double t = 0.0, m = 0.0;
-        for (int k = 0; k < W; k++) {
+        for (int k = 0; k < NW; k++) {
             t += s_ss[k];
             m = fmax(m, s_mx[k]);
         }
@@ -1005,8 +1029,8 @@ __global__ void __launch_bounds__(32 * LYShape<T>::W, ly_minb(R)) k_l2_fy(L2Args
     __threadfence();
     // one warp per grid, whatever the part size, so that the order of the sums is the same
     // however the batch is split into parts
-    const int bpm = D.n[0] / W;
-    for (int k = a.kbeg + w; k < a.kbeg + a.kcnt; k += W) {
+    const int bpm = (DIR == 1 ? D.n[0] : D.nlines(2)) / W;
+    for (int k = a.kbeg + w; k < a.kbeg + a.kcnt; k += NW) {
         double t = 0.0, m = 0.0;
         for (int b = k * bpm + lane; b < (k + 1) * bpm; b += 32) {
             t += __ldcg(a.partial + 2 * b);
@@ -1062,7 +1086,9 @@ static cudaError_t l2_allow_r()
     cudaError_t e;
     if ((e = l2_allow(k_l2_y<T, M, R, 2, NC>)) != cudaSuccess) return e;
     if ((e = l2_allow(k_l2_y<T, M, R, 4, NC>)) != cudaSuccess) return e;
-    if ((e = l2_allow(k_l2_fy<T, M, R, NC>)) != cudaSuccess) return e;
+    if ((e = l2_allow(k_l2_fy<T, M, R, NC, 1>)) != cudaSuccess) return e;
+    if constexpr (NC == 0)
+        if ((e = l2_allow(k_l2_fy<T, M, R, 0, 2>)) != cudaSuccess) return e;
     return l2_allow(k_l2_y0<T, M, R, NC>);
 }
 
@@ -1072,7 +1098,16 @@ static void l2_launch_y(const L2Args<T, M>& a, const PartTab<T>& tb, int which, 
 {
     constexpr int W = LYShape<T>::W;
     if (which == L2_Y0) k_l2_y0<T, M, R, NC><<<nb, 32 * W, sm, st>>>(a, tb);
-    else if (which == L2_FY) k_l2_fy<T, M, R, NC><<<nb, 32 * W, sm, st>>>(a, tb);
+    else if (which == L2_FY) {
+        if constexpr (NC == 0)
+            if (a.fdir == 2) {
+                constexpr int W2 = LFShape<T, 2>::W;
+                const size_t sm2 = ((size_t)W2 * LL<R>::NS + 16 * LFShape<T, 2>::NW) * sizeof(T);
+                k_l2_fy<T, M, R, 0, 2><<<a.D.nlines(2) / W2, 32 * LFShape<T, 2>::NW, sm2, st>>>(a, tb);
+                return;
+            }
+        k_l2_fy<T, M, R, NC, 1><<<nb, 32 * W, sm, st>>>(a, tb);
+    }
     else if (nf == 4) k_l2_y<T, M, R, 4, NC><<<nb, 32 * W, sm, st>>>(a, tb);
     else k_l2_y<T, M, R, 2, NC><<<nb, 32 * W, sm, st>>>(a, tb);
 }
@@ -1102,7 +1137,11 @@ static cudaError_t l2_launch_r(const L2Args<T, M>& a, const PartTab<T>& tb, int 
         else if (nf == 4) k_l2_x<T, M, R, 4><<<nb, 32 * W, sm, st>>>(a, tb);
         else k_l2_x<T, M, R, 2><<<nb, 32 * W, sm, st>>>(a, tb);
     } else {
-        if (which == L2_FY && D.nlines(1) / LYShape<T>::W > a.max_partials) return cudaErrorNotSupported;
+        if (which == L2_FY && a.commit && (a.fdir == 2 ? D.nlines(2) / LFShape<T, 2>::W : D.nlines(1) / LYShape<T>::W) > a.max_partials)
+            return cudaErrorNotSupported;
+        if (which == L2_FY && a.fdir == 2 && (D.n[0] % LFShape<T, 2>::W != 0 ||
+                                              ((size_t)LFShape<T, 2>::W * LL<R>::NS + 16 * LFShape<T, 2>::NW) * sizeof(T) > L2_SMEM_LIMIT))
+            return cudaErrorNotSupported;
         const int nb = a.kcnt * D.n[0] / LYShape<T>::W;   // n0 % W == 0
         if constexpr (NC > 0) {
             if (D.n[1] == NC) {

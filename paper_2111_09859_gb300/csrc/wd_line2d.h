@@ -40,6 +40,8 @@ struct L2Args {
     // max |change|), through per-block partial sums and a fixed-order final reduction
     T cf[6][6];                          // a_m / 2 - alpha_f [m == 1] of the order-2hw member
     int filter;                          // 0: FY only applies the BCs and commits
+    int commit;                          // FY: 1 commit (BCs, norms); 0 filtered field into dst
+    int fdir;                            // FY: line direction, 1 or 2 (3-D)
     T* phin_w;
     double* partial;
     unsigned* counter;                   // zero between launches (the last block resets it)

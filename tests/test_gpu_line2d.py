@@ -145,3 +145,38 @@ def test_line2d_matches_partition_passes(wd, monkeypatch, prec, gname):
     for x, y in zip(out["0"][:2], out["1"][:2]):
         np.testing.assert_allclose(x, y, atol=tol * scale(y), rtol=0)
     assert out["0"][2] == pytest.approx(out["1"][2], rel=1e-8 if prec == 0 else 1e-3)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("eq", [0, 1])
+def test_duct_line_filters_match_oracle(wd, oracle, prec, eq):
+    """Uniform 3-D grids whose lines have partition tables take the line-resident filter passes
+    along directions 0 and 1 (the direction-2 filter with the Dirichlet reset, the change norms
+    and the commit stays on the partition pass): 4 pseudo steps and 10 Poisson steps of a duct
+    128 x 40 x 40 (x periodic) against the oracle, and against the partition passes alone
+    (WD_LINE2D_OFF=1)."""
+    spec = W.duct(40, nx=128)
+    prm = base_params(2, equation=eq)
+    og = oracle_grid(oracle, spec, 2)
+    x, y, z = spec.xyz
+    ex = np.minimum.reduce([y, 1 - y, z, 1 - z])
+    phi0 = og.apply_bc(ex + 0.02 * W.random_field(spec, 21))
+    ref, ost = og.hj_steps(phi0, 4, **oracle_kw(2, prm))
+    refp, _ = og.poisson_steps(np.zeros(spec.N), 10, **oracle_kw(2, prm))
+    tol = 1e-10 if prec == 0 else 1e-5
+    out = {}
+    for off in ("0", "1"):
+        import os
+        os.environ["WD_LINE2D_OFF"] = off
+        try:
+            g = wd.Grid(spec, prec, 2)
+        finally:
+            os.environ.pop("WD_LINE2D_OFF", None)
+        a, st = g.steps(gpu_params(wd, 2, prm), g.as_field(phi0), 4, kind=0)
+        b, _ = g.steps(gpu_params(wd, 2, prm), g.as_field(np.zeros(spec.N)), 10, kind=1)
+        out[off] = (to_np(a), to_np(b), st["res_l2"])
+        g.close()
+    np.testing.assert_allclose(out["0"][0], ref, atol=tol * scale(ref), rtol=0)
+    np.testing.assert_allclose(out["0"][1], refp, atol=tol * scale(refp), rtol=0)
+    assert out["0"][2] == pytest.approx(ost["res_l2"], rel=1e-8 if prec == 0 else 1e-2)
+    np.testing.assert_allclose(out["0"][0], out["1"][0], atol=(1e-11 if prec == 0 else 2e-5) * scale(ref), rtol=0)
