@@ -376,13 +376,13 @@ def run_native(args, rank, world):
 def serving_report(wd, full):
     """Ellipse stream through the request loop (wd_server_*): the closed-loop saturation rate
     of the request mix, then Poisson arrivals at 0.7 x that rate; p50 / p99 latency from
-    submission to completion, throughput.  Default: 24 requests (full: 1000)."""
+    submission to completion, throughput.  Default: 48 requests (full: 1000)."""
     import numpy as np
     import torch
 
     from paper_2111_09859_gb300 import workloads as W
 
-    n = 1000 if full else 24
+    n = 1000 if full else 48
     shapes = W.ellipse_stream(n)
     specs = [W.ellipse(*sh) for sh in shapes]
     p = wd.default_params(wd.C6, equation=wd.HJ_LAD, tol_l2=1e-6, max_iters=20000)
@@ -423,14 +423,14 @@ def serving_report(wd, full):
 def star_report(wd, full):
     """Receding star grain: 1025^2 box, E4 + LAD (Delta x^4 scale), eps 0.15, alpha_f 0.45,
     FP32; the surface recedes by 0.002 per step, each step a warm re-solve on a session grid
-    through the request loop.  Default 100 steps (full: 200).  The burning perimeter of the
+    through the request loop, 200 steps (the configuration's full burn).  The burning perimeter of the
     computed zero level against the marching-squares length of the exact offset field."""
     import numpy as np
     import torch
 
     from paper_2111_09859_gb300 import workloads as W
 
-    steps = 200 if full else 100
+    steps = 200
     sp = W.star(1025)
     h, sd = sp.meta["h"], sp.meta["signed_distance"]
     g = wd.Grid(sp, wd.FP32_METRIC64, wd.E4)
