@@ -951,6 +951,7 @@ struct Solver {
         a.lad = p->equation == WD_HJ_LAD && !poisson;
         a.poisson = poisson;
         a.by = g->tune_by;
+        a.vec = !g->line_off;
         return a;
     }
 

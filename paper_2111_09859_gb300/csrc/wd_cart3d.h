@@ -26,6 +26,7 @@ struct C3Args {
     T eps, cfl, C_lad;
     int equation, lad, stage, poisson;
     int by;                      // block rows of the stencil kernels (0: 8; autotuned)
+    int vec;                     // FP32 3-D: the 4-wide U and stage passes (pitch a multiple of 4)
 };
 
 template <typename T>
