@@ -17,6 +17,7 @@
 
 #include "wd_api_internal.h"
 #include "wd_cart3d.h"
+#include "wd_zfilter.h"
 #include "wd_fused2d.h"
 #include "wd_line2d.h"
 
@@ -89,6 +90,8 @@ struct wd_grid_s {
     std::vector<long long> nact;         // active nodes per stacked grid
     void* w[W_NWORK] = {};
     double* partial = nullptr;
+    void* ztab = nullptr;       // Thomas factors of the filter along direction 2 (3 N values)
+    double ztab_key = -1.0;     // alpha_f they were built for
     unsigned* counter = nullptr;
     double* result = nullptr;
     double* hres = nullptr;     // pinned
@@ -102,6 +105,7 @@ struct wd_grid_s {
     int tuned = 0;              // autotuner ran for this grid
     int tune_stage_threads = 0; // chosen block size of the 2-D stage kernel (0: default)
     int tune_by = 0;            // chosen block rows of the Cartesian stencil kernels (0: default)
+    int tune_zf = 1;            // direction-2 filter + commit of 3-D grids: 1 streamed, 0 partition pass
     int tune_parts = 0;         // chosen number of parts of a stacked batch (line-resident path)
     int cart = 0;               // uniform Cartesian 3-D grid (diagonal constant metrics)
     double h[3] = {0, 0, 0};    // its spacings
@@ -290,6 +294,7 @@ static void release(wd_grid g)
     cudaFree(g->partial);
     cudaFree(g->counter);
     cudaFree(g->result);
+    cudaFree(g->ztab);
     cudaFree(g->dcount);
     if (g->hres) cudaFreeHost(g->hres);
     for (int k = 0; k < 3; k++) {
@@ -398,6 +403,17 @@ struct Solver {
             filter_rows(al, D.n[d], D.per[d], a, c, imp);
             ST(build_line_table(D.n[d], D.per[d], a, c, imp, t));
             t.key = al;
+            g->gen++;
+        }
+        if (D.ndim == 3 && !D.per[2] && g->ztab_key != al) {
+            // the streamed direction-2 pass: the filter rows' Thomas factors in the state precision
+            const int N = D.n[2];
+            std::vector<double> f(3 * (size_t)N);
+            zfilter_factors(al, N, f.data());
+            std::vector<T> ft(f.begin(), f.end());
+            if (!g->ztab) CK(cudaMalloc(&g->ztab, 3 * (size_t)N * sizeof(double)));
+            CK(cudaMemcpy(g->ztab, ft.data(), ft.size() * sizeof(T), cudaMemcpyHostToDevice));
+            g->ztab_key = al;
             g->gen++;
         }
         return WD_OK;
@@ -967,6 +983,61 @@ struct Solver {
         return (long long)D.nlines(2) / 32 <= g->npartial;
     }
 
+    // the direction-2 filter with the commit streamed along z (wd_zfilter.cu)
+    bool zfilter_ok() const
+    {
+        return p->filter && g->ztab && g->ztab_key == p->alpha_f && zfilter_supported(D, g->npartial);
+    }
+    ZfArgs<T> zf_args(bool poisson)
+    {
+        ZfArgs<T> z;
+        std::memset(&z, 0, sizeof(z));
+        z.D = D;
+        z.src = W(W_PHIS);
+        z.scratch = W(W_T0);
+        z.phin = W(W_PHIN);
+        z.phin_w = W(W_PHIN);
+        z.mask = g->mask;
+        z.dval = (const T*)g->dval;
+        z.poisson = poisson;
+        z.tab = (const T*)g->ztab;
+        LineOp op;
+        op_filter(p->alpha_f, op);
+        for (int hw = 1; hw <= 5; hw++)
+            for (int m = 1; m <= hw; m++) z.cf[hw][m] = T(0.5 * op.fa[hw][m] - (m == 1 ? p->alpha_f : 0.0));
+        z.partial = g->partial;
+        z.result = g->result;
+        z.max_partials = g->npartial;
+        return z;
+    }
+
+    // the partition pass that filters along direction 2 of a 3-D grid and commits
+    F2Args<T, M> commit2_args(bool poisson)
+    {
+        F2Args<T, M> f;
+        std::memset(&f, 0, sizeof(f));
+        f.D = D;
+        f.src = W(W_PHIS);
+        f.dst = W(W_PHIS);
+        f.phin = W(W_PHIN);
+        f.phin_w = W(W_PHIN);
+        f.mask = g->mask;
+        f.dval = (const T*)g->dval;
+        f.bclo1 = f.bchi1 = WD_BC_WALL;
+        f.poisson = poisson;
+        f.filter = 1;
+        f.alpha_f = p->alpha_f;
+        f.partial = g->partial;
+        f.counter = g->counter;
+        f.result = g->result;
+        f.max_partials = g->npartial;
+        f.batch = 1;
+        LineOp op;
+        op_filter(p->alpha_f, op);
+        std::memcpy(f.fa, op.fa, sizeof(f.fa));
+        return f;
+    }
+
     wd_status step_cart3d(bool poisson)
     {
         if (p->filter) ST(ensure_filter(p->alpha_f));
@@ -1011,27 +1082,12 @@ struct Solver {
                 l.fdir = 1;
                 CK(l2_launch<T, M>(l, g->ftab[1].template pview<T>(), L2_FY, 2, st));
             }
-            F2Args<T, M> f;
-            std::memset(&f, 0, sizeof(f));
-            f.D = D;
-            f.src = W(W_PHIS);
-            f.dst = W(W_PHIS);
-            f.phin = W(W_PHIN);
-            f.phin_w = W(W_PHIN);
-            f.mask = g->mask;
-            f.dval = (const T*)g->dval;
-            f.bclo1 = f.bchi1 = WD_BC_WALL;
-            f.poisson = poisson;
-            f.filter = 1;
-            f.alpha_f = p->alpha_f;
-            f.partial = g->partial;
-            f.counter = g->counter;
-            f.result = g->result;
-            f.max_partials = g->npartial;
-            f.batch = 1;
-            LineOp op;
-            ST(op_filter(p->alpha_f, op));
-            std::memcpy(f.fa, op.fa, sizeof(f.fa));
+            if (g->tune_zf && zfilter_ok()) {
+                ProfScope ps(g, WD_K_NORM);
+                CK(zfilter_commit<T>(zf_args(poisson), st));
+                return WD_OK;
+            }
+            const F2Args<T, M> f = commit2_args(poisson);
             const PartTab<T> t2 = g->ftab[2].template pview<T>();
             if (p2_supported(f, t2, F2_FILTER, 2)) {
                 ProfScope ps(g, WD_K_NORM);
@@ -1277,6 +1333,18 @@ struct Solver {
                     c3_launch<T>(a, C3_S, st);
                 });
             });
+            if (p->filter && line3_filters()) {
+                // the direction-2 filter + commit: streamed along z (1) or the partition pass
+                // (0); both overwrite phi^n, which begin() sets after this
+                ST(ensure_filter(p->alpha_f));
+                const F2Args<T, M> f = commit2_args(false);
+                const PartTab<T> t2 = g->ftab[2].template pview<T>();
+                if (zfilter_ok() && p2_supported(f, t2, F2_FILTER, 2))
+                    g->tune_zf = tune_choice(std::string(key) + ":zf", {1, 0}, [&](int c) {
+                        if (c) return time_calls(st, [&] { zfilter_commit<T>(zf_args(false), st); });
+                        return time_calls(st, [&] { p2_launch<T, M>(f, t2, F2_FILTER, 2, st); });
+                    });
+            }
         }
         CK(cudaGetLastError());
         return WD_OK;

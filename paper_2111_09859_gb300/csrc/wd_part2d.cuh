@@ -246,9 +246,41 @@ __global__ void __launch_bounds__(32 * LPB, P2_MINB(T, LPB)) k_p2_filter(F2Args<
         if (hw >= 1 && mm >= 1 && mm <= hw) v = 0.5 * a.fa[hw][mm] - (mm == 1 ? a.alpha_f : 0.0);
         cf[hw][mm] = T(v);
     }
-    // every global load of the pass happens here (the commit epilogue then only stores), so
-    // that the loads of a thread's nodes are in flight together
-    if (commit)
+    // every global load of the pass happens here (the commit epilogue then only stores).  Off
+    // direction 0 a thread's nodes (at most R: rows tid / LPB + 32 k of one line) are loaded
+    // into registers first, so that their loads are in flight together, then stored
+    if (dir != 0) {
+        const int l = tid & (LPB - 1), i0 = tid / LPB;
+        if (l < nl) {
+            const long long st = D.stride(dir), base = D.line_base(dir, q0 + l);
+            T v[R], o[R];
+            uint8_t m[R];
+#pragma unroll
+            for (int k = 0; k < R; k++) {
+                const int i = i0 + 32 * k;
+                if (i < N) {
+                    const long long e = base + (long long)i * st;
+                    v[k] = a.src[e];
+                    if (commit) {
+                        o[k] = a.phin[e];
+                        m[k] = a.mask[e];
+                    }
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < R; k++) {
+                const int i = i0 + 32 * k;
+                if (i < N) {
+                    const int s = l * Lay::LS + Lay::at(i);
+                    A[s] = v[k];
+                    if (commit) {
+                        O[s] = o[k];
+                        MK[s] = m[k];
+                    }
+                }
+            }
+        }
+    } else if (commit)
         p2_nodes<LPB>(D, dir, q0, nl, [&](int l, int i, long long e) {
             const int s = l * Lay::LS + Lay::at(i);
             A[s] = a.src[e];

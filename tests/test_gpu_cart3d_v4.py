@@ -8,7 +8,8 @@ on grids that exercise the split between 4-wide groups and per-node fallbacks:
   - row lengths that are not multiples of 4 (ragged groups; a periodic row of 10 runs every
     node on the per-node bodies) and a periodic row of 8 (both groups at the wrap, their
     neighbour groups taken from the other end of the row);
-  - non-periodic faces in x, y and z (the fallback's closure rows), and periodic z."""
+  - non-periodic faces in x, y and z (the fallback's closure rows), and periodic z;
+and the streamed direction-2 filter with the commit (wd_zfilter.cu) in FP64 and FP32."""
 import numpy as np
 import pytest
 
@@ -79,6 +80,7 @@ def test_cart3d_v4_steps_match_oracle(wd, oracle, monkeypatch, name):
     ref, ost = og.hj_steps(phi0, 4, **oracle_kw(scheme, prm))
     refp, _ = og.poisson_steps(np.zeros(spec.N), 10, **oracle_kw(scheme, prm))
     out = {}
+    monkeypatch.setenv("WD_AUTOTUNE", "0")   # default shapes: the streamed direction-2 filter where it applies
     for off in ("0", "1"):
         monkeypatch.setenv("WD_LINE2D_OFF", off)
         g = wd.Grid(spec, wd.FP32, scheme)
@@ -91,3 +93,29 @@ def test_cart3d_v4_steps_match_oracle(wd, oracle, monkeypatch, name):
     assert out["0"][2] == pytest.approx(ost["res_l2"], rel=1e-2)
     np.testing.assert_allclose(out["0"][0], out["1"][0], atol=2e-6 * scale(ref), rtol=0)
     np.testing.assert_allclose(out["0"][1], out["1"][1], atol=2e-6 * scale(refp), rtol=0)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("name", ["duct64x40-E6-lad", "box96x40x24-walls-E6-std"])
+def test_streamed_z_filter_matches_oracle(wd, oracle, monkeypatch, prec, name):
+    """The filter along direction 2 fused with the commit and streamed along z (wd_zfilter.cu:
+    a Thomas sweep per column, forward into scratch, backward with the Dirichlet reset, the
+    commit and the change norms), which the grids whose rows are a multiple of 32 long take
+    by default: 4 pseudo steps and 10 Poisson steps against the oracle at the step bars
+    (1e-10 FP64, 1e-5 FP32), and the residual of the last step."""
+    mk, per, scheme, eq = CASES[name]
+    spec = mk()
+    prm = base_params(scheme, equation=eq)
+    og = oracle_grid(oracle, spec, scheme)
+    phi0 = og.apply_bc(wall_distance(spec, per) + 0.02 * W.random_field(spec, 8))
+    ref, ost = og.hj_steps(phi0, 4, **oracle_kw(scheme, prm))
+    refp, _ = og.poisson_steps(np.zeros(spec.N), 10, **oracle_kw(scheme, prm))
+    monkeypatch.setenv("WD_AUTOTUNE", "0")
+    g = wd.Grid(spec, prec, scheme)
+    out, st = g.steps(gpu_params(wd, scheme, prm), g.as_field(phi0), 4, kind=0)
+    outp, _ = g.steps(gpu_params(wd, scheme, prm), g.as_field(np.zeros(spec.N)), 10, kind=1)
+    g.close()
+    tol = 1e-10 if prec == 0 else 1e-5
+    np.testing.assert_allclose(to_np(out), ref, atol=tol * scale(ref), rtol=0)
+    np.testing.assert_allclose(to_np(outp), refp, atol=tol * scale(refp), rtol=0)
+    assert st["res_l2"] == pytest.approx(ost["res_l2"], rel=1e-8 if prec == 0 else 1e-2)
