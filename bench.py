@@ -593,6 +593,29 @@ def duct_report(wd):
     ev1.record()
     torch.cuda.synchronize()
     ms = ev0.elapsed_time(ev1) / 20
+    # per-pass device time (the library's CUDA-event timer around each launch) against the
+    # pass's algorithmic bytes per node (every array it must touch read once, every output
+    # written once; stage: LAD, averaged over the four RK stages)
+    g.profile(True)
+    g.steps(p, phi, 4)
+    prof = g.profile_read()
+    g.profile(False)
+    peak = peak_hbm()[0]
+    per_node = {"deriv": ("U: phi in; U_0..2 and C|LAD| out", 20),
+                "gauss": ("Gaussian of C|LAD| along x and y", 8),
+                "point": ("RK stage: U_0..2, G, phi, phi^n, flags, dt and acc in; stage, acc (dt) out", 39),
+                "filter": ("filters along x and y (one timed scope): field in and out, twice", 16),
+                "norm": ("filter along z + commit: field, phi^n, flags in; phi^n out", 13)}
+    kernels = {}
+    for cls, (what, b) in per_node.items():
+        tot, n = prof.get(cls, (0.0, 0))
+        if not n:
+            continue
+        launches = n   # timed scopes
+        us = tot / launches * 1e3
+        gbs = b * sp.N / (us * 1e-6) / 1e9
+        kernels[cls] = {"what": what, "us_per_launch": round(us, 1), "launches_per_step": round(launches / 4, 2),
+                        "bytes_per_node": b, "GBps": round(gbs, 1), "frac_of_measured_hbm": round(gbs / peak, 3)}
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     out, st = g.solve(p)
@@ -602,7 +625,7 @@ def duct_report(wd):
     g.close()
     return {"nodes": sp.N, "ms_per_step": round(ms, 3), "mcell_iter_s": round(sp.N / (ms * 1e-3) / 1e6, 1),
             "solve_s": round(ts, 3), "solve_iters": st["iters"] + st["poisson_iters"],
-            "max_err_vs_exact": float("%.3g" % err)}
+            "max_err_vs_exact": float("%.3g" % err), "kernels": kernels}
 
 
 def cpu_baseline(n_steps=12):
