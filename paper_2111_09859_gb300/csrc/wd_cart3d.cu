@@ -210,12 +210,23 @@ __device__ __forceinline__ int halo_index(int u, int N, int per)
     return u > N - 1 ? 2 * (N - 1) - u : u;
 }
 
-constexpr int GXY_TY = 32;   // tile rows (4 per thread of a 32 x 8 block)
+constexpr int GXY_TY = 32;   // tile rows (4 consecutive per thread of a 32 x 8 block)
+constexpr int GXY_LS = 44;   // row stride of the tile + halo (40 used; 16-byte rows)
 
+template <typename T>
+__device__ __forceinline__ T gauss9(const T* v)   // v[0..8] centred on v[4]
+{
+    return T(3565.0 / 10368.0) * v[4] + T(3091.0 / 12960.0) * (v[5] + v[3]) + T(1997.0 / 25920.0) * (v[6] + v[2]) +
+           T(149.0 / 12960.0) * (v[7] + v[1]) + T(107.0 / 103680.0) * (v[8] + v[0]);
+}
+
+// Each smoothing phase gives a thread 4 neighbouring outputs from a 12-value window in
+// registers: along x 4 consecutive columns of a row (three 16-byte shared loads in FP32),
+// along y 4 consecutive rows of a column.
 template <typename T>
 __global__ void __launch_bounds__(256) k_c3_gauss_xy(C3Args<T> a)
 {
-    __shared__ T Ls[GXY_TY + 8][41];
+    __shared__ __align__(16) T Ls[GXY_TY + 8][GXY_LS];
     __shared__ T Gx[GXY_TY + 8][33];
     const Dims& D = a.D;
     const int i0 = blockIdx.x * 32, j0 = blockIdx.y * GXY_TY, k = blockIdx.z;
@@ -229,17 +240,14 @@ __global__ void __launch_bounds__(256) k_c3_gauss_xy(C3Args<T> a)
     if constexpr (std::is_same<T, float>::value)
         vec = a.vec && (D.per[0] ? D.n[0] % 4 == 0 : (i0 >= 4 && i0 + 36 <= D.n[0]));
     if (vec) {
-        for (int q = tid; q < (GXY_TY + 8) * 10; q += 256) {
-            const int r = q / 10, c4 = q - r * 10;
-            const int gj = halo_index<T>(j0 - 4 + r, D.n[1], D.per[1]);
-            int gx = i0 - 4 + 4 * c4;
-            if (D.per[0]) gx = ((gx % D.n[0]) + D.n[0]) % D.n[0];
-            const float4 v = __ldg(reinterpret_cast<const float4*>(Lk + gx + st1 * gj));
-            Ls[r][4 * c4] = v.x;
-            Ls[r][4 * c4 + 1] = v.y;
-            Ls[r][4 * c4 + 2] = v.z;
-            Ls[r][4 * c4 + 3] = v.w;
-        }
+        if constexpr (std::is_same<T, float>::value)
+            for (int q = tid; q < (GXY_TY + 8) * 10; q += 256) {
+                const int r = q / 10, c4 = q - r * 10;
+                const int gj = halo_index<T>(j0 - 4 + r, D.n[1], D.per[1]);
+                int gx = i0 - 4 + 4 * c4;
+                if (D.per[0]) gx = ((gx % D.n[0]) + D.n[0]) % D.n[0];
+                *reinterpret_cast<float4*>(&Ls[r][4 * c4]) = __ldg(reinterpret_cast<const float4*>(Lk + gx + st1 * gj));
+            }
     } else {
         for (int q = tid; q < (GXY_TY + 8) * 40; q += 256) {
             const int r = q / 40, c = q - r * 40;
@@ -249,25 +257,35 @@ __global__ void __launch_bounds__(256) k_c3_gauss_xy(C3Args<T> a)
         }
     }
     __syncthreads();
-    const T c0 = T(3565.0 / 10368.0), c1 = T(3091.0 / 12960.0), c2 = T(1997.0 / 25920.0), c3 = T(149.0 / 12960.0),
-            c4 = T(107.0 / 103680.0);
-    for (int q = tid; q < (GXY_TY + 8) * 32; q += 256) {
-        const int r = q >> 5, c = q & 31;
-        const T* v = &Ls[r][c];
-        Gx[r][c] = c0 * v[4] + c1 * (v[5] + v[3]) + c2 * (v[6] + v[2]) + c3 * (v[7] + v[1]) + c4 * (v[8] + v[0]);
+    // along x: rows 0 .. GXY_TY + 7, columns 4 c4 .. 4 c4 + 3 (c4 < 8)
+    for (int q = tid; q < (GXY_TY + 8) * 8; q += 256) {
+        const int r = q >> 3, c4 = q & 7;
+        T v[12];
+        if constexpr (std::is_same<T, float>::value) {
+#pragma unroll
+            for (int u = 0; u < 3; u++) {
+                const float4 t = *reinterpret_cast<const float4*>(&Ls[r][4 * c4 + 4 * u]);
+                v[4 * u] = t.x, v[4 * u + 1] = t.y, v[4 * u + 2] = t.z, v[4 * u + 3] = t.w;
+            }
+        } else {
+#pragma unroll
+            for (int u = 0; u < 12; u++) v[u] = Ls[r][4 * c4 + u];
+        }
+#pragma unroll
+        for (int u = 0; u < 4; u++) Gx[r][4 * c4 + u] = gauss9(v + u);
     }
     __syncthreads();
+    // along y: column threadIdx.x, rows 4 threadIdx.y .. 4 threadIdx.y + 3 of the tile
     const int i = i0 + threadIdx.x;
     if (i >= D.n[0]) return;
-    const int c = threadIdx.x;
+    const int c = threadIdx.x, r0 = 4 * threadIdx.y;
+    T v[12];
 #pragma unroll
-    for (int rr = 0; rr < GXY_TY / 8; rr++) {
-        const int j = j0 + threadIdx.y + 8 * rr;
-        if (j >= D.n[1]) break;
-        const int r = threadIdx.y + 8 * rr + 4;
-        const T g = c0 * Gx[r][c] + c1 * (Gx[r + 1][c] + Gx[r - 1][c]) + c2 * (Gx[r + 2][c] + Gx[r - 2][c]) +
-                    c3 * (Gx[r + 3][c] + Gx[r - 3][c]) + c4 * (Gx[r + 4][c] + Gx[r - 4][c]);
-        a.G2[i + st1 * j + (size_t)st2 * k] = g;
+    for (int u = 0; u < 12; u++) v[u] = Gx[r0 + u][c];
+#pragma unroll
+    for (int u = 0; u < 4; u++) {
+        const int j = j0 + r0 + u;
+        if (j < D.n[1]) a.G2[i + st1 * j + (size_t)st2 * k] = gauss9(v + u);
     }
 }
 
