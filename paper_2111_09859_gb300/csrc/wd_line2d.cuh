@@ -897,20 +897,20 @@ __global__ void __launch_bounds__(32 * LXShape<T>::W) k_l2_fx(L2Args<T, M> a, Pa
 // nodes), the commit of the new state and the change norms, else the filtered field into dst
 // Direction-2 lines of a 3-D grid lie a whole plane apart: their blocks take 32 neighbouring
 // lines (128-byte row segments), each warp solving 32 / NW of them.
-template <typename T, int DIR>
+template <typename T, int DIR, bool WIDE = false>
 struct LFShape {
-    static constexpr int NW = LYShape<T>::W;                     // warps per block
-    static constexpr int W = DIR == 2 ? 32 : LYShape<T>::W;      // lines per block
+    static constexpr int NW = LYShape<T>::W;                             // warps per block
+    static constexpr int W = (DIR == 2 || WIDE) ? 32 : LYShape<T>::W;    // lines per block
 };
 
-template <typename T, typename M, int R, int NC, int DIR>
-__global__ void __launch_bounds__(32 * LFShape<T, DIR>::NW, ly_minb(R)) k_l2_fy(L2Args<T, M> a, PartTab<T> tb)
+template <typename T, typename M, int R, int NC, int DIR, bool WIDE = false>
+__global__ void __launch_bounds__(32 * LFShape<T, DIR, WIDE>::NW, ly_minb(R)) k_l2_fy(L2Args<T, M> a, PartTab<T> tb)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
-    __shared__ double s_ss[LFShape<T, DIR>::NW], s_mx[LFShape<T, DIR>::NW];
+    __shared__ double s_ss[LFShape<T, DIR, WIDE>::NW], s_mx[LFShape<T, DIR, WIDE>::NW];
     __shared__ int s_last;
     using L = LL<R>;
-    constexpr int W = LFShape<T, DIR>::W, NW = LFShape<T, DIR>::NW, VW = VecT<T>::n;
+    constexpr int W = LFShape<T, DIR, WIDE>::W, NW = LFShape<T, DIR, WIDE>::NW, VW = VecT<T>::n;
     constexpr int TPR = W / VW;                 // threads per row segment
     constexpr int JS = 32 * NW / TPR;           // rows per sweep
     const Dims& D = a.D;
@@ -1089,7 +1089,19 @@ static cudaError_t l2_allow_r()
     if ((e = l2_allow(k_l2_fy<T, M, R, NC, 1>)) != cudaSuccess) return e;
     if constexpr (NC == 0)
         if ((e = l2_allow(k_l2_fy<T, M, R, 0, 2>)) != cudaSuccess) return e;
+    if constexpr (NC == 0)
+        if ((e = l2_allow(k_l2_fy<T, M, R, 0, 1, true>)) != cudaSuccess) return e;
     return l2_allow(k_l2_y0<T, M, R, NC>);
+}
+
+// whether a direction-1 filter pass takes the 32-line blocks: a 3-D grid, no commit, rows of a
+// multiple of 32 nodes, the lines' shared memory within the limit
+template <typename T, int R, typename A>
+static bool l2_fy_wide(const A& a)
+{
+    using S = LFShape<T, 1, true>;
+    return a.D.ndim == 3 && !a.commit && a.fdir == 1 && a.D.n[0] % S::W == 0 && a.kbeg == 0 &&
+           a.kcnt == a.D.n[2] && ((size_t)S::W * LL<R>::NS + 16 * S::NW) * sizeof(T) <= L2_SMEM_LIMIT;
 }
 
 template <typename T, typename M, int R, int NC>
@@ -1104,6 +1116,13 @@ static void l2_launch_y(const L2Args<T, M>& a, const PartTab<T>& tb, int which, 
                 constexpr int W2 = LFShape<T, 2>::W;
                 const size_t sm2 = ((size_t)W2 * LL<R>::NS + 16 * LFShape<T, 2>::NW) * sizeof(T);
                 k_l2_fy<T, M, R, 0, 2><<<a.D.nlines(2) / W2, 32 * LFShape<T, 2>::NW, sm2, st>>>(a, tb);
+                return;
+            } else if (l2_fy_wide<T, R>(a)) {
+                // 3-D direction 1 without the commit: 32 lines per block, so that every row
+                // access is a 128-byte segment (the lines' rows lie a whole x-row apart)
+                using S = LFShape<T, 1, true>;
+                const size_t sm3 = ((size_t)S::W * LL<R>::NS + 16 * S::NW) * sizeof(T);
+                k_l2_fy<T, M, R, 0, 1, true><<<a.D.nlines(1) / S::W, 32 * S::NW, sm3, st>>>(a, tb);
                 return;
             }
         k_l2_fy<T, M, R, NC, 1><<<nb, 32 * W, sm, st>>>(a, tb);
