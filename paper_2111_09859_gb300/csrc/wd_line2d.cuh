@@ -1089,19 +1089,20 @@ static cudaError_t l2_allow_r()
     if ((e = l2_allow(k_l2_fy<T, M, R, NC, 1>)) != cudaSuccess) return e;
     if constexpr (NC == 0)
         if ((e = l2_allow(k_l2_fy<T, M, R, 0, 2>)) != cudaSuccess) return e;
-    if constexpr (NC == 0)
-        if ((e = l2_allow(k_l2_fy<T, M, R, 0, 1, true>)) != cudaSuccess) return e;
+    if ((e = l2_allow(k_l2_fy<T, M, R, NC, 1, true>)) != cudaSuccess) return e;
     return l2_allow(k_l2_y0<T, M, R, NC>);
 }
 
-// whether a direction-1 filter pass takes the 32-line blocks: a 3-D grid, no commit, rows of a
-// multiple of 32 nodes, the lines' shared memory within the limit
+// whether a direction-1 filter pass takes the 32-line blocks: rows of a multiple of 32 nodes
+// (a block's lines are then consecutive nodes of one row of one grid) and lines of at most 17
+// rows per lane (longer lines: too few blocks, one per SM; the 1025-node radial lines of the
+// 1025 x 2048 ellipse measured 47 us against 38 us with 8 lines per block)
 template <typename T, int R, typename A>
 static bool l2_fy_wide(const A& a)
 {
     using S = LFShape<T, 1, true>;
-    return a.D.ndim == 3 && !a.commit && a.fdir == 1 && a.D.n[0] % S::W == 0 && a.kbeg == 0 &&
-           a.kcnt == a.D.n[2] && ((size_t)S::W * LL<R>::NS + 16 * S::NW) * sizeof(T) <= L2_SMEM_LIMIT;
+    return R <= 17 && a.fdir == 1 && a.D.n[0] % S::W == 0 &&
+           ((size_t)S::W * LL<R>::NS + 16 * S::NW) * sizeof(T) <= L2_SMEM_LIMIT;
 }
 
 template <typename T, typename M, int R, int NC>
@@ -1117,14 +1118,15 @@ static void l2_launch_y(const L2Args<T, M>& a, const PartTab<T>& tb, int which, 
                 const size_t sm2 = ((size_t)W2 * LL<R>::NS + 16 * LFShape<T, 2>::NW) * sizeof(T);
                 k_l2_fy<T, M, R, 0, 2><<<a.D.nlines(2) / W2, 32 * LFShape<T, 2>::NW, sm2, st>>>(a, tb);
                 return;
-            } else if (l2_fy_wide<T, R>(a)) {
-                // 3-D direction 1 without the commit: 32 lines per block, so that every row
-                // access is a 128-byte segment (the lines' rows lie a whole x-row apart)
-                using S = LFShape<T, 1, true>;
-                const size_t sm3 = ((size_t)S::W * LL<R>::NS + 16 * S::NW) * sizeof(T);
-                k_l2_fy<T, M, R, 0, 1, true><<<a.D.nlines(1) / S::W, 32 * S::NW, sm3, st>>>(a, tb);
-                return;
             }
+        if (l2_fy_wide<T, R>(a)) {
+            // 32 lines per block, so that every row access is a 128-byte segment (the lines'
+            // rows lie a whole x-row apart)
+            using S = LFShape<T, 1, true>;
+            const size_t sm3 = ((size_t)S::W * LL<R>::NS + 16 * S::NW) * sizeof(T);
+            k_l2_fy<T, M, R, NC, 1, true><<<a.kcnt * a.D.n[0] / S::W, 32 * S::NW, sm3, st>>>(a, tb);
+            return;
+        }
         k_l2_fy<T, M, R, NC, 1><<<nb, 32 * W, sm, st>>>(a, tb);
     }
     else if (nf == 4) k_l2_y<T, M, R, 4, NC><<<nb, 32 * W, sm, st>>>(a, tb);
