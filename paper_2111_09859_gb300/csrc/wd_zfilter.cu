@@ -5,16 +5,16 @@
 // Direction 2 is the slowest in memory: its lines' nodes lie a whole plane apart.  Instead of
 // staging lines in shared memory, one thread takes one (i, j) column and walks its z-line
 // while the threads of a block hold up to 256 neighbouring columns of a row, so every access
-// of a warp is a 128-byte row segment and a block's accesses to a plane one contiguous run.  The filter system a_t x_{t-1} + x_t + c_t x_{t+1} = d_t (delta form: d_t the
-// right-hand side of second differences, x_t = fh_t - f_t) is solved by the Thomas algorithm
-// with factors computed once on the host:
+// of a warp is a 128-byte row segment and a block's accesses to a plane one contiguous run.
+// The filter system a_t x_{t-1} + x_t + c_t x_{t+1} = d_t (delta form: d_t the right-hand
+// side of second differences, x_t = fh_t - f_t) is solved by the Thomas algorithm with factors
+// computed once on the host:
 //   forward  (t = 0 .. N-1):  y_t = (d_t - a_t y_{t-1}) / m_t      -> scratch
 //   backward (t = N-1 .. 0):  x_t = y_t - c'_t x_{t+1},  fh_t = f_t + x_t, then the commit.
 // Each sweep loads its next chunk of planes (16 forward, 8 backward) while it computes the
 // current one, so that loads stay in flight across the whole sweep.  (Four columns per thread
-// with 16-byte accesses measured slower: a quarter of the threads keeps fewer loads in
-// flight.)  The right-hand side and the
-// epilogue are those of the line passes: the order-2hw member with hw = min(5, distance to
+// with 16-byte accesses, and chunks twice as long, measured slower.)  The right-hand side and
+// the epilogue are those of the line passes: the order-2hw member with hw = min(5, distance to
 // the nearer end), end nodes unfiltered; Dirichlet nodes take their values (0 in the Poisson
 // phase); the squared changes of the other nodes are summed per block in double (per thread
 // over chunks of 8 nodes in the state precision), the blocks in a fixed order.
