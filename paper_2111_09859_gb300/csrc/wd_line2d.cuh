@@ -49,6 +49,10 @@ struct LL {
     static constexpr int G = (H + R - 1) / R;            // ghost blocks per side
     static constexpr int S = (R % 2 == 0) ? R + 1 : R;
     static constexpr int NS = (32 + 2 * G) * S;          // slots of one line buffer
+    // line-buffer stride of the direction-1 passes, whose two threads per row segment take
+    // lines 4 apart (16 bytes of lines each): NSY = 4 (mod 8) puts the two halves of a warp
+    // on disjoint halves of the banks
+    static constexpr int NSY = NS + ((12 - NS % 8) % 8);
     static constexpr int fdiv(int a) { return a >= 0 ? a / R : -((R - 1 - a) / R); }
     // slot offset of row k + m of a lane's block from the block's first slot
     static constexpr int off(int km) { return fdiv(km) * S + (km - fdiv(km) * R); }
@@ -558,8 +562,8 @@ __global__ void __launch_bounds__(32 * LYShape<T>::W, ly_minb(R)) k_l2_y(L2Args<
     const int q0 = a.kbeg * D.n[0] + blockIdx.x * W;
     const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
     T* sm = reinterpret_cast<T*>(smraw);
-    auto buf = [&](int b, int l) { return sm + (size_t)(b * W + l) * L::NS; };
-    T* scr = sm + (size_t)NBUF * W * L::NS + 16 * w;
+    auto buf = [&](int b, int l) { return sm + (size_t)(b * W + l) * L::NSY; };
+    T* scr = sm + (size_t)NBUF * W * L::NSY + 16 * w;
     const long long tot = D.total, st = D.pitch;
     const M* xi = a.xi;
     const bool lad = a.lad;
@@ -771,8 +775,8 @@ __global__ void __launch_bounds__(32 * LYShape<T>::W, ly_minb(R)) k_l2_y0(L2Args
     const int q0 = a.kbeg * D.n[0] + blockIdx.x * W;
     const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
     T* sm = reinterpret_cast<T*>(smraw);
-    auto buf = [&](int b, int l) { return sm + (size_t)(b * W + l) * L::NS; };
-    T* scr = sm + (size_t)3 * W * L::NS + 16 * w;
+    auto buf = [&](int b, int l) { return sm + (size_t)(b * W + l) * L::NSY; };
+    T* scr = sm + (size_t)3 * W * L::NSY + 16 * w;
     const long long tot = D.total, st = D.pitch;
     const bool lad = a.lad;
     const int lv0 = (tid & 1) * VW;
@@ -1065,8 +1069,8 @@ static size_t l2_smem(int which, int nf)
     if (which == L2_X) return (size_t)LXShape<T>::W * ((nf + 1) * l2_ns<R>() + 16) * sizeof(T);
     if (which == L2_FX) return (size_t)LXShape<T>::W * (l2_ns<R>() + 16) * sizeof(T);
     if (which == L2_FY) return ((size_t)LYShape<T>::W * l2_ns<R>() + 16 * LYShape<T>::W) * sizeof(T);
-    if (which == L2_Y) return ((size_t)(nf == 4 ? 6 : 4) * LYShape<T>::W * l2_ns<R>() + 16 * LYShape<T>::W) * sizeof(T);
-    return ((size_t)3 * LYShape<T>::W * l2_ns<R>() + 16 * LYShape<T>::W) * sizeof(T);
+    if (which == L2_Y) return ((size_t)(nf == 4 ? 6 : 4) * LYShape<T>::W * LL<R>::NSY + 16 * LYShape<T>::W) * sizeof(T);
+    return ((size_t)3 * LYShape<T>::W * LL<R>::NSY + 16 * LYShape<T>::W) * sizeof(T);
 }
 
 template <typename K>
