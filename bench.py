@@ -116,7 +116,7 @@ def peak_hbm():
 # DRAM bytes (read + write) per launch of the dominant kernel class, from one ncu capture of
 # the current kernel on this workload (profiles/k_l2_passes_cylinder_batch16.md): k_l2_y, the
 # direction-1 pass of an RK stage, stage 2 (120.2 MB read + 14.2 MB written).
-PROFILED_TRAFFIC = {"line1": 134.36e6}
+PROFILED_TRAFFIC = {"line1": 131.3e6}
 
 
 def algorithmic_bytes(cls, nodes, nd, es, ms, curv, lad=True):
